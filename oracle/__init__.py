@@ -1,0 +1,238 @@
+"""CPU oracle for the paper's local stereo method (arXiv 2212.00488).
+
+TEST INFRASTRUCTURE ONLY: only the test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package. The library's
+product path never calls it and it never calls the library.
+
+The arithmetic lives in ``stereo_oracle.c`` (plain C, direct loops); this
+module only marshals numpy arrays and strings the stages together in the order
+of Sec. III of the paper:
+
+  grey -> (downscale, Eq. 2) -> census + arms -> cost (Eqs. 3-6)
+  -> aggregation along x then y (Eqs. 7-8) -> WTA (Eq. 9), both bases
+  -> cross-check (Eq. 10) -> median -> bilateral fill (Eq. 11) -> (upscale)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.oracle_grey.argtypes = [_u8p, _int, _int, _u8p]
+        L.oracle_downscale.argtypes = [_u8p, _int, _int, _u8p]
+        L.oracle_census.argtypes = [_u8p, _int, _int, _u8p]
+        L.oracle_arms.argtypes = [_u8p, _int, _int, _int, _int, _int, _u8p, _u8p, _u8p, _u8p]
+        L.oracle_cost_tables.argtypes = [_dbl, _dbl, _int, _i32p, _i32p]
+        L.oracle_volume_int.argtypes = [_u8p] * 8 + [_int] * 4 + [_i32p, _i32p, ctypes.c_void_p, _i64p]
+        L.oracle_volume_int.restype = _int
+        L.oracle_wta_int.argtypes = [_u8p] * 8 + [_int] * 4 + [_i32p, _i32p, _u8p, ctypes.c_void_p]
+        L.oracle_wta_int.restype = _int
+        L.oracle_wta_f64.argtypes = [_u8p] * 8 + [_int] * 4 + [_dbl, _dbl, _u8p, _f64p, _f64p]
+        L.oracle_wta_f64.restype = _int
+        L.oracle_crosscheck.argtypes = [_u8p, _u8p, _int, _int, _u8p]
+        L.oracle_median3.argtypes = [_u8p, _int, _int, _u8p]
+        L.oracle_fill.argtypes = [_u8p, _u8p, _u8p, _int, _int, _int, _f32p]
+        L.oracle_upscale.argtypes = [_f32p, _u8p, _u8p, _int, _int, _int, _int, _int, _f32p]
+        _lib = L
+    return _lib
+
+
+@dataclass
+class Params:
+    """The method's constants (Sec. V and the Table II footnote) and readings."""
+    lambda_ad: float = 0.3
+    lambda_mc: float = 2.3
+    tc: int = 13          # brightness threshold delta of the arms
+    wx: int = 21          # horizontal arm cap per side
+    wy: int = 31          # vertical arm cap per side
+    t_fill: int = 3       # T of the bilateral estimation
+    downscale: int = 1    # 1: K = 2, m = 1 mean-pool and Dmax halved; 0: none
+    cost_scale: int = 512  # integer mode: each cost term is round(scale * value)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def grey(rgb):
+    rgb = _c(rgb, np.uint8)
+    H, W = rgb.shape[:2]
+    out = np.empty((H, W), np.uint8)
+    lib().oracle_grey(rgb, W, H, out)
+    return out
+
+
+def downscale(g):
+    g = _c(g, np.uint8)
+    H, W = g.shape
+    out = np.empty((H // 2, W // 2), np.uint8)
+    lib().oracle_downscale(g, W, H, out)
+    return out
+
+
+def census(g):
+    g = _c(g, np.uint8)
+    Y, X = g.shape
+    out = np.empty((Y, X), np.uint8)
+    lib().oracle_census(g, X, Y, out)
+    return out
+
+
+def arms(g, wx=21, wy=31, tc=13):
+    """Returns (hm, hp, vm, vp), each uint8 [Y][X]."""
+    g = _c(g, np.uint8)
+    Y, X = g.shape
+    hm, hp, vm, vp = (np.empty((Y, X), np.uint8) for _ in range(4))
+    lib().oracle_arms(g, X, Y, wx, wy, tc, hm, hp, vm, vp)
+    return hm, hp, vm, vp
+
+
+def cost_tables(lambda_ad=0.3, lambda_mc=2.3, scale=512):
+    ad = np.empty(256, np.int32)
+    mc = np.empty(7, np.int32)
+    lib().oracle_cost_tables(lambda_ad, lambda_mc, scale, ad, mc)
+    return ad, mc
+
+
+def _base_args(gB, cB, gM, cM, armsB):
+    hm, hp, vm, vp = armsB
+    return [_c(gB, np.uint8), _c(cB, np.uint8), _c(gM, np.uint8), _c(cM, np.uint8),
+            _c(hm, np.uint8), _c(hp, np.uint8), _c(vm, np.uint8), _c(vp, np.uint8)]
+
+
+def volume_int(gB, cB, gM, cM, armsB, D, direction, p: Params = Params(), want_cost=False):
+    """Aggregated volume CA[d][y][x] (int64) of one base; optionally the cost C too.
+
+    direction -1: left base (match at x - d); +1: right base (match at x + d)."""
+    Y, X = np.shape(gB)
+    ad, mc = cost_tables(p.lambda_ad, p.lambda_mc, p.cost_scale)
+    CA = np.empty((D, Y, X), np.int64)
+    C = np.empty((D, Y, X), np.int64) if want_cost else None
+    rc = lib().oracle_volume_int(*_base_args(gB, cB, gM, cM, armsB), X, Y, D, direction, ad, mc,
+                                 C.ctypes.data if C is not None else None, CA)
+    if rc != 0:
+        raise MemoryError("oracle_volume_int")
+    return (CA, C) if want_cost else CA
+
+
+def wta_int(gB, cB, gM, cM, armsB, D, direction, p: Params = Params(), want_best=False):
+    Y, X = np.shape(gB)
+    ad, mc = cost_tables(p.lambda_ad, p.lambda_mc, p.cost_scale)
+    disp = np.empty((Y, X), np.uint8)
+    best = np.empty((Y, X), np.int64) if want_best else None
+    rc = lib().oracle_wta_int(*_base_args(gB, cB, gM, cM, armsB), X, Y, D, direction, ad, mc, disp,
+                              best.ctypes.data if best is not None else None)
+    if rc != 0:
+        raise MemoryError("oracle_wta_int")
+    return (disp, best) if want_best else disp
+
+
+def wta_f64(gB, cB, gM, cM, armsB, D, direction, p: Params = Params()):
+    """FP64 mode: returns (disp, best, second) with the two lowest CA per pixel."""
+    Y, X = np.shape(gB)
+    disp = np.empty((Y, X), np.uint8)
+    best = np.empty((Y, X), np.float64)
+    second = np.empty((Y, X), np.float64)
+    rc = lib().oracle_wta_f64(*_base_args(gB, cB, gM, cM, armsB), X, Y, D, direction,
+                              p.lambda_ad, p.lambda_mc, disp, best, second)
+    if rc != 0:
+        raise MemoryError("oracle_wta_f64")
+    return disp, best, second
+
+
+def crosscheck(dl, dr):
+    dl = _c(dl, np.uint8)
+    Y, X = dl.shape
+    out = np.empty((Y, X), np.uint8)
+    lib().oracle_crosscheck(dl, _c(dr, np.uint8), X, Y, out)
+    return out
+
+
+def median3(d):
+    d = _c(d, np.uint8)
+    Y, X = d.shape
+    out = np.empty((Y, X), np.uint8)
+    lib().oracle_median3(d, X, Y, out)
+    return out
+
+
+def fill(dm, gcp, g, T=3):
+    dm = _c(dm, np.uint8)
+    Y, X = dm.shape
+    out = np.empty((Y, X), np.float32)
+    lib().oracle_fill(dm, _c(gcp, np.uint8), _c(g, np.uint8), X, Y, T, out)
+    return out
+
+
+def upscale(dp, gs, gf, T=3):
+    dp = _c(dp, np.float32)
+    Y, X = dp.shape
+    H, W = np.shape(gf)
+    out = np.empty((H, W), np.float32)
+    lib().oracle_upscale(dp, _c(gs, np.uint8), _c(gf, np.uint8), X, Y, W, H, T, out)
+    return out
+
+
+def processed_dmax(dmax: int, downscale: int) -> int:
+    """Disparity count after scaling down: Dmax is halved (Sec. I), rounded up."""
+    return (dmax + 1) // 2 if downscale else dmax
+
+
+@dataclass
+class Result:
+    disp: np.ndarray          # final float map (full-res units and size when downscaled)
+    dl: np.ndarray            # D^L uint8 at processed size
+    dr: np.ndarray            # D^R uint8
+    gcp: np.ndarray           # GCP mask uint8 (0/1)
+    dm: np.ndarray            # median-filtered D^L
+    dplus: np.ndarray         # filled map, float, processed size and units
+    grey_l: np.ndarray        # processed grey images
+    grey_r: np.ndarray
+    census_l: np.ndarray
+    census_r: np.ndarray
+    arms_l: tuple
+    arms_r: tuple
+    grey_full_l: np.ndarray = field(default=None)
+
+
+def pipeline(left_rgb, right_rgb, dmax: int, p: Params = Params()) -> Result:
+    """The whole method (Sec. III steps 1-8) on one RGB pair, integer cost mode."""
+    gl_full, gr_full = grey(left_rgb), grey(right_rgb)
+    if p.downscale:
+        gl, gr = downscale(gl_full), downscale(gr_full)
+    else:
+        gl, gr = gl_full, gr_full
+    D = processed_dmax(dmax, p.downscale)
+    cl, cr = census(gl), census(gr)
+    al = arms(gl, p.wx, p.wy, p.tc)
+    ar = arms(gr, p.wx, p.wy, p.tc)
+    dl = wta_int(gl, cl, gr, cr, al, D, -1, p)
+    dr = wta_int(gr, cr, gl, cl, ar, D, +1, p)
+    gcp = crosscheck(dl, dr)
+    dm = median3(dl)
+    dplus = fill(dm, gcp, gl, p.t_fill)
+    if p.downscale:
+        disp = upscale(dplus, gl, gl_full, p.t_fill)
+    else:
+        disp = dplus.copy()
+    return Result(disp, dl, dr, gcp, dm, dplus, gl, gr, cl, cr, al, ar, gl_full)
