@@ -1,0 +1,308 @@
+"""Throughput of the stereo pipeline on the paper's workload shape.
+
+Workload: one RGB pair of 1436 x 992 with Dmax 145 per step (the paper's
+Adirondack(H) shape, Table II), downscaled 2x to 718 x 496 with D = 73, the
+whole pipeline of Sec. III including the bilateral upscale. Inputs are seeded
+synthetic piecewise-planar scenes (the Middlebury images are not available).
+
+value: frames per second over K back-to-back steps with inputs resident in
+HBM, timed with CUDA events on the stream the library launches on; the inputs
+rotate over a pool of pairs larger than the L2 cache. e2e: the same metric
+through the host-buffer entry point (host-to-device copies of both images and
+the device-to-host copy of the float map inside the timed region).
+roofline: the fused cost + aggregation + WTA kernel against the SM issue
+limit (ALU-bound; see the design doc for the per-cell operation count).
+
+Multi-GPU (torchrun): one independent replica per GPU on its own frames
+(weak scaling); a barrier and a max over ranks bracket the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fps & W·H·D/s at 1436×992, Dmax 145 on 1 GB300; % of HBM/ALU roofline"
+W_FULL, H_FULL, DMAX = 1436, 992, 145
+PLANES, SEED = 40, 0
+POOL = 20                       # 20 pairs x 8.5 MB = 171 MB > 126 MB of L2
+PAPER_FPS = 40.0                # Table II, GTX 780 Ti (context only)
+OPS_PER_CELL = 13               # algorithmic integer operations per (x, y, d) cell, both bases
+SM_COUNT_NOMINAL = 152
+LANES_PER_SM = 128              # 4 SM sub-partitions x 32 lanes issue one warp instruction per clock each
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores: a bounded sample per step."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2212_00488_gb300 import scenes
+    oracle.build.build()
+    s = scenes.make_scene(W_FULL, H_FULL, DMAX, PLANES, SEED)
+    band = H_FULL // 8                            # 124 full-res rows per step
+    fracs, times = [], []
+    for i in range(args.warmup + args.steps):
+        y0 = (i * band) % (H_FULL - band)
+        l, r = s.left[y0:y0 + band], s.right[y0:y0 + band]
+        t0 = time.perf_counter()
+        oracle.pipeline(np.ascontiguousarray(l), np.ascontiguousarray(r), DMAX, oracle.Params())
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            fracs.append(band / H_FULL)
+    total = sum(times)
+    fps = sum(fracs) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": "1436x992 RGB, Dmax 145, downscale 2x (718x496, D 73), full pipeline",
+                   "sample": f"{band}-row band of the frame per step"},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one {band}x{W_FULL} row band (1/8 frame) per step, single thread, "
+                                   "scaled to frames/s"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_leg():
+    """The oracle timed on this host (rank 0, N = 1): two full frames, one thread."""
+    import numpy as np
+
+    import oracle
+    from paper_2212_00488_gb300 import scenes
+    oracle.build.build()
+    s = scenes.make_scene(W_FULL, H_FULL, DMAX, PLANES, SEED)
+    n, t0 = 2, time.perf_counter()
+    for _ in range(n):
+        oracle.pipeline(np.ascontiguousarray(s.left), np.ascontiguousarray(s.right), DMAX, oracle.Params())
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full 1436x992/145 frames, whole pipeline, single thread"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2212_00488_gb300 import Stereo, _lib, build, scenes
+    build.build()
+
+    pool = scenes.scene_pool(W_FULL, H_FULL, DMAX, PLANES, SEED + rank, POOL)
+    left = [torch.from_numpy(p.left).to(dev) for p in pool]
+    right = [torch.from_numpy(p.right).to(dev) for p in pool]
+    st = Stereo(local)
+    out = st(left[0], right[0], DMAX)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        st(left[i % POOL], right[i % POOL], DMAX, out=out)
+    torch.cuda.synchronize()
+
+    _lib.stereo_set_profiling(st.ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record(stream)
+    for i in range(args.steps):
+        st(left[i % POOL], right[i % POOL], DMAX, out=out)
+        launches += _lib.stereo_last_launch_count(st.ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    stage_ms, nframes = _lib.stereo_stage_ms(st.ctx)
+    _lib.stereo_set_profiling(st.ctx, False)
+
+    t_local = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    fps = world * args.steps / (ms_max / 1e3)
+
+    # e2e through the host-buffer entry point, pinned host memory
+    hl = [torch.from_numpy(p.left).pin_memory() for p in pool[:4]]
+    hr = [torch.from_numpy(p.right).pin_memory() for p in pool[:4]]
+    hdisp = torch.empty((H_FULL, W_FULL), dtype=torch.float32).pin_memory()
+    for i in range(3):
+        st.compute_host(hl[i % 4], hr[i % 4], DMAX, hdisp)
+    e2e_steps = max(10, min(args.steps, 100))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        st.compute_host(hl[i % 4], hr[i % 4], DMAX, hdisp)
+    e2e_dt = time.perf_counter() - t0
+    t_e2e = torch.tensor([e2e_dt], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_fps = world * e2e_steps / float(t_e2e.item())
+
+    if rank == 0:
+        peaks, src = _peaks()
+        X, Y, D = W_FULL // 2, H_FULL // 2, (DMAX + 1) // 2
+        cells = X * Y * D
+        t_hot = stage_ms[_lib.STAGE_COSTAGG] / 1e3
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak_ops = sm_count * LANES_PER_SM * sm_mhz * 1e6
+        achieved = OPS_PER_CELL * cells / t_hot
+        line = {
+            "metric": METRIC,
+            "value": fps,
+            "unit": "frames/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": fps / world / PAPER_FPS,
+            "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "1436x992 RGB pair, Dmax 145, downscaled 2x to 718x496 with D 73, "
+                                   "full pipeline (grey, downscale, census+arms, cost+aggregation+WTA both "
+                                   "bases, cross-check, median, bilateral fill, upscale)",
+                       "scene": "seeded piecewise-planar, 40 planes, texture sigma 20, sensor sigma 2",
+                       "l2": f"inputs rotate over {POOL} pairs ({POOL * W_FULL * H_FULL * 6 / 1e6:.0f} MB > L2)",
+                       "parallelism": f"replicas x{world}",
+                       "vs_baseline_ref": "paper Table II: 40 fps on a GTX 780 Ti (context, other hardware)"},
+            "mde_per_s": fps * W_FULL * H_FULL * DMAX,
+            "stage_ms": dict(zip(_lib.STAGE_NAMES, [round(t, 5) for t in stage_ms])),
+            "roofline": {"bound": "alu", "kernel": "costagg_wta_kernel", "achieved": achieved / 1e12,
+                         "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": achieved / peak_ops,
+                         "traffic": None,
+                         "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz (issue limit, "
+                                        f"max clock from {src} peaks)",
+                         "ops_per_cell": OPS_PER_CELL, "cells_per_launch": cells,
+                         "kernel_ms": stage_ms[_lib.STAGE_COSTAGG], "frames_timed": nframes},
+            "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 2 * W_FULL * H_FULL * 3,
+                    "d2h_bytes_per_step": W_FULL * H_FULL * 4, "steps": e2e_steps,
+                    "timer": "host wall clock around the synchronous host-buffer call"},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_leg()
+        print(json.dumps(line), flush=True)
+    st.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * C ABI of the GB300 (sm_103a) implementation of the local stereo method of
+ * Chang & Maruyama, "Real-Time High-Quality Stereo Matching System on a GPU"
+ * (arXiv 2212.00488).
+ *
+ * Pipeline (Sec. III, steps 1-8): grey -> 2x mean-pool downscale (Eq. 2) ->
+ * mini-census + cross arms -> matching cost AD + mini-census (Eqs. 3-6) ->
+ * cross-based aggregation along x then y (Eqs. 7-8) -> winner-take-all for
+ * the left and right base images (Eq. 9) -> GCP cross-check (Eq. 10) ->
+ * median filter -> bilateral estimation fill (Eq. 11) -> upscale (Step 8).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns STEREO_OK (0) or a negative STEREO_E* code and
+ *    never throws; stereo_last_error() then holds a one-line reason.
+ *  - Images are RGB, uint8, HWC interleaved, row pitch 3*W bytes, no padding.
+ *  - Buffers named "device" are CUDA device (or managed) memory that the
+ *    caller owns and keeps alive until the work on the stream has finished.
+ *    The context owns only its workspace.
+ *  - Work is asynchronous on the given stream (NULL = the context's own
+ *    stream); synchronise that stream, or call stereo_sync(), before reading.
+ *  - Dmax counts disparities: d in [0, Dmax-1] (Sec. II). With downscaling,
+ *    the processed image is (W/2) x (H/2) and D = ceil(Dmax/2) (Sec. I);
+ *    processed-size maps (dl, dr, gcp) hold processed-resolution disparities,
+ *    and the final float map holds full-resolution disparities.
+ *  - A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef STEREO_H
+#define STEREO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STEREO_API __attribute__((visibility("default")))
+
+enum {
+    STEREO_OK = 0,
+    STEREO_EINVAL = -1,   /* bad argument: size, pointer, parameter or stage */
+    STEREO_ENOMEM = -2,   /* the workspace would exceed the context's memory cap, or allocation failed */
+    STEREO_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    STEREO_ETIMEOUT = -4  /* a bounded device-side wait gave up */
+};
+
+/* Pipeline stages, in order, as reported by stereo_stage_ms() (the columns of
+ * Table II, with W+- and W*+- merged into one support stage). */
+enum {
+    STEREO_STAGE_SCALEDOWN = 0, /* grey + mean-pool downscale (SD) */
+    STEREO_STAGE_SUPPORT = 1,   /* mini-census codes and the four cross arms (W+-, W*+-) */
+    STEREO_STAGE_COSTAGG = 2,   /* fused cost + x/y aggregation + WTA, both bases (C+CA_x, CA) */
+    STEREO_STAGE_REFINE = 3,    /* cross-check + median + bilateral fill (CC, Post) */
+    STEREO_STAGE_UPSCALE = 4,   /* scale-up (SU) */
+    STEREO_NUM_STAGES = 5
+};
+
+/* Method parameters. Defaults (stereo_default_params) are the paper's values
+ * (Sec. V: lambda_AD = 0.3, lambda_MC = 2.3, T = 3; Table II footnote:
+ * W_x = 21, W_y = 31 per side, TC = 13) plus this build's readings. */
+typedef struct {
+    double lambda_ad; /* Eq. 4, on intensities scaled to [0, 1]; 0.3 */
+    double lambda_mc; /* Eq. 5; 2.3 */
+    int tc;           /* arm brightness threshold delta (strict <), Sec. III-C; 13 */
+    int wx;           /* horizontal arm cap per side, 1..29; 21 */
+    int wy;           /* vertical arm cap per side, 1..31; 31 */
+    int t_fill;       /* T of the bilateral estimation (Sec. III-E); 3 */
+    int downscale;    /* 1: K = 2, m = 1 mean-pool with Dmax halved (Sec. III-A); 0: none */
+    int cost_scale;   /* integer cost mode: each term is round(cost_scale * value); 512.
+                         (2*wx+1)*(2*wy+1)*(AD(255)+MC(6)) must stay below 2^24. */
+} stereo_params;
+
+typedef struct stereo_ctx stereo_ctx;
+
+/* Fills *out with the defaults listed above. */
+STEREO_API void stereo_default_params(stereo_params *out);
+
+/* Creates a context bound to CUDA device `device` with its own non-blocking
+ * stream. p = NULL takes the defaults; a copy of *p is kept. mem_cap_bytes
+ * bounds the device workspace the context may allocate (0 = no cap).
+ * Returns EINVAL for a NULL out, bad parameters or a device that is not
+ * sm_103; ECUDA when the device cannot be initialised. On failure *out is NULL. */
+STEREO_API int stereo_create(stereo_ctx **out, int device, const stereo_params *p,
+                             size_t mem_cap_bytes);
+
+/* Releases the workspace, stream and context. NULL is a no-op. Waits for the
+ * context's own stream first. */
+STEREO_API void stereo_destroy(stereo_ctx *ctx);
+
+/* One-line description of the last failure on this context ("" if none). The
+ * string belongs to the context and stays valid until its next call. */
+STEREO_API const char *stereo_last_error(const stereo_ctx *ctx);
+
+/* The whole method on one pair (Sec. III steps 1-8).
+ *  left_rgb, right_rgb: device, H*W*3 bytes each.
+ *  W, H: input size, 1..8192 each; with downscaling both must be >= 2.
+ *  Dmax: 1..256 without downscaling, 1..511 with it (D <= 256 after halving).
+ *  disp_out: device float, required. With downscaling: H*W full-resolution
+ *    disparities (Step 8 output); without: H*W filled map D+ (Step 7 output).
+ *  dl_out, dr_out: optional (NULL to skip) device uint8 [Y][X] winner-take-all
+ *    maps D^L, D^R of the processed image (Eq. 9), X*Y bytes each.
+ *  gcp_out: optional device uint8 [Y][X], 1 where Eq. 10 holds, else 0.
+ *  stream: cudaStream_t or NULL for the context's stream.
+ * The workspace grows on demand (ENOMEM past the cap). Asynchronous. */
+STEREO_API int stereo_compute(stereo_ctx *ctx, const uint8_t *left_rgb, const uint8_t *right_rgb,
+                              int W, int H, int Dmax, float *disp_out, uint8_t *dl_out,
+                              uint8_t *dr_out, uint8_t *gcp_out, void *stream);
+
+/* stereo_compute on HOST buffers: copies the two images in, runs the
+ * pipeline, copies the float map (and the optional uint8 maps) back and waits
+ * for the stream. Sizes and layouts as for stereo_compute; every pointer is
+ * host memory (pinned memory makes the copies asynchronous-capable and faster).
+ * Uses a device staging area inside the workspace. Synchronous. */
+STEREO_API int stereo_compute_host(stereo_ctx *ctx, const uint8_t *left_rgb, const uint8_t *right_rgb,
+                                   int W, int H, int Dmax, float *disp_out, uint8_t *dl_out,
+                                   uint8_t *dr_out, uint8_t *gcp_out);
+
+/* Blocks until all work on the context's own stream has finished. */
+STEREO_API int stereo_sync(stereo_ctx *ctx);
+
+/* Copies intermediates of the last stereo_compute on this context into device
+ * buffers (any may be NULL), enqueued on `stream` after that compute:
+ *  grey_l, grey_r: uint8 [Y][X] processed grey images (after Eq. 2);
+ *  census_l, census_r: uint8 [Y][X] six-bit mini-census codes, bit k for the
+ *    neighbour (dx,dy) = (-1,-1),(+1,-1),(-2,0),(+2,0),(-1,+1),(+1,+1) darker;
+ *  arms_l, arms_r: uint32 [Y][X], bytes (low to high) = left, right, up, down
+ *    arm lengths (m, n, M, N of Eqs. 7-8);
+ *  dm: uint8 [Y][X] median-filtered D^L; dplus: float [Y][X] filled map D+.
+ * Returns EINVAL when no compute has run. */
+STEREO_API int stereo_debug_planes(stereo_ctx *ctx, uint8_t *grey_l, uint8_t *grey_r,
+                                   uint8_t *census_l, uint8_t *census_r, uint32_t *arms_l,
+                                   uint32_t *arms_r, uint8_t *dm, float *dplus, void *stream);
+
+/* Re-launches one stage (STEREO_STAGE_*) of the last stereo_compute on this
+ * context, with the same inputs, outputs and workspace, on `stream`. Used to
+ * time a single kernel. The caller keeps the last compute's buffers alive.
+ * Returns EINVAL when no compute has run or the stage is out of range. */
+STEREO_API int stereo_launch_stage(stereo_ctx *ctx, int stage, void *stream);
+
+/* Turns per-stage timing on (1) or off (0) and clears the accumulated times.
+ * When on, every stereo_compute records CUDA events between its stages on its
+ * stream; the events of a frame are read back only when their slot in a ring
+ * of 64 is reused, so profiling adds no synchronisation between frames. */
+STEREO_API int stereo_set_profiling(stereo_ctx *ctx, int on);
+
+/* Mean per-stage device times (ms) over every compute profiled since
+ * profiling was turned on, waiting for the outstanding events. ms must hold n
+ * entries, n <= STEREO_NUM_STAGES; a stage that did not run reports 0.
+ * Returns the number of frames averaged (>= 1), or EINVAL when none was
+ * profiled. */
+STEREO_API int stereo_stage_ms(stereo_ctx *ctx, float *ms, int n);
+
+/* Number of kernels (memsets excluded) the last stereo_compute launched. */
+STEREO_API int stereo_last_launch_count(const stereo_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STEREO_H */

@@ -1,0 +1,59 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stereo {
+
+// Packed per-pixel words written by the support stage and read by the fused
+// cost/aggregation kernel:
+//   pix = grey | census << 8                       (uint32, bits 14..31 zero)
+//   arm = left | right << 8 | up << 16 | down << 24 (uint32, arm lengths)
+__host__ __device__ inline uint32_t pack_arm(int hm, int hp, int vm, int vp)
+{
+    return (uint32_t)hm | ((uint32_t)hp << 8) | ((uint32_t)vm << 16) | ((uint32_t)vp << 24);
+}
+
+// Tile shape of the fused kernel (see costagg.cu).
+constexpr int kRing = 64;      // V-prefix ring depth: 2*wy + 2 <= 64
+constexpr int kMaxWy = 31;
+constexpr int kMaxWx = 29;
+
+struct CostAggArgs {
+    const uint32_t *pix_l, *pix_r;   // [Y][X]
+    const uint32_t *arm_l, *arm_r;   // [Y][X]
+    uint32_t *key_l, *key_r;         // [Y][X] min over d of (CA << 8 | d); preset to ~0
+    const uint32_t *lut;             // [256 * 8] combined cost table, index ad * 8 + hamming
+    int X, Y, D;
+    int wx, wy;
+    uint32_t P;                      // cost of a match outside the image
+};
+
+// Launchers (each returns the launch error, cudaSuccess on success).
+cudaError_t launch_grey(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t *g_l, uint8_t *g_r,
+                        int W, int H, cudaStream_t s);
+cudaError_t launch_downscale(const uint8_t *g_l, const uint8_t *g_r, uint8_t *s_l, uint8_t *s_r,
+                             int W, int H, cudaStream_t s);
+// Also presets the WTA keys of both bases to ~0 for the fused kernel.
+cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix_l, uint32_t *pix_r,
+                           uint32_t *arm_l, uint32_t *arm_r, uint32_t *key_l, uint32_t *key_r,
+                           int X, int Y, int wx, int wy, int tc, cudaStream_t s);
+cudaError_t launch_costagg(const CostAggArgs &a, cudaStream_t s);
+cudaError_t launch_refine(const uint32_t *key_l, const uint32_t *key_r, const uint8_t *grey_l,
+                          int X, int Y, int T, uint8_t *dl, uint8_t *dr, uint8_t *gcp, uint8_t *dm,
+                          float *dplus, cudaStream_t s);
+cudaError_t launch_upscale(const float *dplus, const uint8_t *grey_low, const uint8_t *grey_full,
+                           int X, int Y, int W, int H, int T, float *out, cudaStream_t s);
+cudaError_t launch_unpack_planes(const uint32_t *pix, const uint32_t *arm, uint8_t *grey,
+                                 uint8_t *census, uint32_t *arms, int X, int Y, cudaStream_t s);
+
+// Shared-memory bytes the fused kernel needs for wx (0 if unsupported).
+size_t costagg_smem_bytes(int wx);
+
+// One-time per-device function attributes (large dynamic shared memory);
+// call with the device current.
+cudaError_t costagg_setup();
+cudaError_t refine_setup();
+
+}  // namespace stereo

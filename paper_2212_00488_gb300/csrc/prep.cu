@@ -1,0 +1,180 @@
+// Preprocessing kernels: grey conversion (Sec. III step 1), 2x mean-pool
+// downscale (Sec. III-A, Eq. 2), and the per-pixel support data of the fused
+// kernel: mini-census code (Sec. III-B) and the four cross arms (Sec. III-C).
+// All of these are memory-bound passes over a few MB; each pixel is read from
+// HBM once and the neighbourhoods are staged in shared memory.
+#include "internal.cuh"
+
+namespace stereo {
+namespace {
+
+__device__ __forceinline__ uint32_t luma(uint32_t r, uint32_t g, uint32_t b)
+{
+    // Step 1 gives no formula: BT.601 weights in 8-bit fixed point, rounded.
+    return (77u * r + 150u * g + 29u * b + 128u) >> 8;
+}
+
+// RGB (HWC) -> grey for both images (blockIdx.y selects the image). Each
+// thread converts four consecutive pixels; with a 4-byte aligned source those
+// twelve bytes are three aligned 32-bit loads.
+template <bool kAligned>
+__global__ void grey_kernel(const uint8_t *__restrict__ rgb_l, const uint8_t *__restrict__ rgb_r,
+                            uint8_t *__restrict__ g_l, uint8_t *__restrict__ g_r, long n)
+{
+    const uint8_t *rgb = blockIdx.y ? rgb_r : rgb_l;
+    uint8_t *g = blockIdx.y ? g_r : g_l;
+    long p = 4 * ((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (p >= n) return;
+    if (kAligned && p + 4 <= n) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(rgb + 3 * p);
+        uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2);
+        // byte order: w0 = r0 g0 b0 r1 | w1 = g1 b1 r2 g2 | w2 = b2 r3 g3 b3
+        uint32_t y0 = luma(w0 & 0xFF, (w0 >> 8) & 0xFF, (w0 >> 16) & 0xFF);
+        uint32_t y1 = luma(w0 >> 24, w1 & 0xFF, (w1 >> 8) & 0xFF);
+        uint32_t y2 = luma((w1 >> 16) & 0xFF, w1 >> 24, w2 & 0xFF);
+        uint32_t y3 = luma((w2 >> 8) & 0xFF, (w2 >> 16) & 0xFF, w2 >> 24);
+        *reinterpret_cast<uint32_t *>(g + p) = y0 | (y1 << 8) | (y2 << 16) | (y3 << 24);
+    } else {
+        for (long q = p; q < p + 4 && q < n; ++q)
+            g[q] = (uint8_t)luma(rgb[3 * q], rgb[3 * q + 1], rgb[3 * q + 2]);
+    }
+}
+
+// Eq. 2 with K = 2, m = 1: mean of the 3x3 window centred on (2x, 2y),
+// coordinates clamped to the image, rounded half up: (sum + 4) / 9.
+__global__ void downscale_kernel(const uint8_t *__restrict__ g_l, const uint8_t *__restrict__ g_r,
+                                 uint8_t *__restrict__ s_l, uint8_t *__restrict__ s_r, int W, int H)
+{
+    const uint8_t *g = blockIdx.z ? g_r : g_l;
+    uint8_t *s = blockIdx.z ? s_r : s_l;
+    int X = W / 2, Y = H / 2;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    if (x >= X || y >= Y) return;
+    int sum = 0;
+#pragma unroll
+    for (int j = -1; j <= 1; ++j) {
+        int yy = min(max(2 * y + j, 0), H - 1);
+        const uint8_t *row = g + (size_t)yy * W;
+#pragma unroll
+        for (int i = -1; i <= 1; ++i) sum += __ldg(row + min(max(2 * x + i, 0), W - 1));
+    }
+    s[(size_t)y * X + x] = (uint8_t)((sum + 4) / 9);
+}
+
+constexpr int kSupTX = 64;   // output tile of the support kernel
+constexpr int kSupTY = 8;
+constexpr int kSupNT = 256;
+
+// Mini-census code and cross arms of every pixel of one image (blockIdx.z).
+// The tile plus a halo of max(wx, 2) columns and max(wy, 1) rows is staged in
+// shared memory with clamped coordinates; census reads the clamped copies
+// (border replication), while the arm scans stop at the real image border.
+__global__ void __launch_bounds__(kSupNT) support_kernel(
+    const uint8_t *__restrict__ g_l, const uint8_t *__restrict__ g_r,
+    uint32_t *__restrict__ pix_l, uint32_t *__restrict__ pix_r,
+    uint32_t *__restrict__ arm_l, uint32_t *__restrict__ arm_r,
+    uint32_t *__restrict__ key_l, uint32_t *__restrict__ key_r,
+    int X, int Y, int wx, int wy, int tc)
+{
+    extern __shared__ uint8_t tile[];
+    const uint8_t *g = blockIdx.z ? g_r : g_l;
+    uint32_t *pix = blockIdx.z ? pix_r : pix_l;
+    uint32_t *arm = blockIdx.z ? arm_r : arm_l;
+    uint32_t *key = blockIdx.z ? key_r : key_l;
+    const int hx = max(wx, 2), hy = max(wy, 1);
+    const int TW = kSupTX + 2 * hx, TH = kSupTY + 2 * hy;
+    const int x0 = blockIdx.x * kSupTX, y0 = blockIdx.y * kSupTY;
+
+    for (int i = threadIdx.x; i < TW * TH; i += kSupNT) {
+        int ty = i / TW, tx = i - ty * TW;
+        int gx = min(max(x0 - hx + tx, 0), X - 1);
+        int gy = min(max(y0 - hy + ty, 0), Y - 1);
+        tile[i] = __ldg(g + (size_t)gy * X + gx);
+    }
+    __syncthreads();
+
+    // Census pattern (Fig. 3 is missing): six neighbours in rows y-1..y+1,
+    // mirror-symmetric in x; bit k set when neighbour k is strictly darker.
+    const int cdx[6] = {-1, +1, -2, +2, -1, +1};
+    const int cdy[6] = {-1, -1, 0, 0, +1, +1};
+
+    for (int o = threadIdx.x; o < kSupTX * kSupTY; o += kSupNT) {
+        int oy = o / kSupTX, ox = o - oy * kSupTX;
+        int x = x0 + ox, y = y0 + oy;
+        if (x >= X || y >= Y) continue;
+        const int tx = ox + hx, ty = oy + hy;
+        const uint8_t *t = tile + ty * TW + tx;
+        int c = t[0];
+        uint32_t code = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) code |= (uint32_t)(t[cdy[k] * TW + cdx[k]] < c) << k;
+        int hm = 0, hp = 0, vm = 0, vp = 0;
+        while (hm < wx && x - hm - 1 >= 0 && abs((int)t[-(hm + 1)] - c) < tc) ++hm;
+        while (hp < wx && x + hp + 1 < X && abs((int)t[hp + 1] - c) < tc) ++hp;
+        while (vm < wy && y - vm - 1 >= 0 && abs((int)t[-(vm + 1) * TW] - c) < tc) ++vm;
+        while (vp < wy && y + vp + 1 < Y && abs((int)t[(vp + 1) * TW] - c) < tc) ++vp;
+        size_t idx = (size_t)y * X + x;
+        pix[idx] = (uint32_t)c | (code << 8);
+        arm[idx] = pack_arm(hm, hp, vm, vp);
+        key[idx] = 0xFFFFFFFFu;   // WTA key preset: the fused kernel takes atomic minima
+    }
+}
+
+__global__ void unpack_kernel(const uint32_t *__restrict__ pix, const uint32_t *__restrict__ arm,
+                              uint8_t *grey, uint8_t *census, uint32_t *arms, long n)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t p = pix[i];
+    if (grey) grey[i] = (uint8_t)(p & 0xFF);
+    if (census) census[i] = (uint8_t)((p >> 8) & 0x3F);
+    if (arms) arms[i] = arm[i];
+}
+
+}  // namespace
+
+cudaError_t launch_grey(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t *g_l, uint8_t *g_r,
+                        int W, int H, cudaStream_t s)
+{
+    long n = (long)W * H;
+    long quads = (n + 3) / 4;
+    dim3 grid((unsigned)((quads + 255) / 256), 2);
+    bool aligned = ((reinterpret_cast<uintptr_t>(rgb_l) | reinterpret_cast<uintptr_t>(rgb_r)) & 3) == 0;
+    if (aligned)
+        grey_kernel<true><<<grid, 256, 0, s>>>(rgb_l, rgb_r, g_l, g_r, n);
+    else
+        grey_kernel<false><<<grid, 256, 0, s>>>(rgb_l, rgb_r, g_l, g_r, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_downscale(const uint8_t *g_l, const uint8_t *g_r, uint8_t *s_l, uint8_t *s_r,
+                             int W, int H, cudaStream_t s)
+{
+    int X = W / 2, Y = H / 2;
+    dim3 grid((X + 127) / 128, Y, 2);
+    downscale_kernel<<<grid, 128, 0, s>>>(g_l, g_r, s_l, s_r, W, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix_l, uint32_t *pix_r,
+                           uint32_t *arm_l, uint32_t *arm_r, uint32_t *key_l, uint32_t *key_r,
+                           int X, int Y, int wx, int wy, int tc, cudaStream_t s)
+{
+    const int hx = wx > 2 ? wx : 2, hy = wy > 1 ? wy : 1;
+    size_t smem = (size_t)(kSupTX + 2 * hx) * (kSupTY + 2 * hy);
+    dim3 grid((X + kSupTX - 1) / kSupTX, (Y + kSupTY - 1) / kSupTY, 2);
+    support_kernel<<<grid, kSupNT, smem, s>>>(g_l, g_r, pix_l, pix_r, arm_l, arm_r, key_l, key_r, X, Y, wx,
+                                               wy, tc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_planes(const uint32_t *pix, const uint32_t *arm, uint8_t *grey,
+                                 uint8_t *census, uint32_t *arms, int X, int Y, cudaStream_t s)
+{
+    long n = (long)X * Y;
+    unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pix, arm, grey, census, arms, n);
+    return cudaGetLastError();
+}
+
+}  // namespace stereo
