@@ -182,8 +182,11 @@ def run_ours(args):
     left = [torch.from_numpy(p.left).to(dev) for p in pool]
     right = [torch.from_numpy(p.right).to(dev) for p in pool]
     st = Stereo(local)
+    if args.tile >= 0:
+        _lib.stereo_set_tile(st.ctx, args.tile)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     out = st(left[0], right[0], DMAX)
-    stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize()
 
     for i in range(args.warmup):
@@ -273,7 +276,8 @@ def run_ours(args):
                          "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz (issue limit, "
                                         f"max clock from {src} peaks)",
                          "ops_per_cell": OPS_PER_CELL, "cells_per_launch": cells,
-                         "kernel_ms": stage_ms[_lib.STAGE_COSTAGG], "frames_timed": nframes},
+                         "kernel_ms": stage_ms[_lib.STAGE_COSTAGG], "frames_timed": nframes,
+                         "tile": _lib.stereo_get_tile(st.ctx, W_FULL, H_FULL, DMAX)},
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 2 * W_FULL * H_FULL * 3,
                     "d2h_bytes_per_step": W_FULL * H_FULL * 4, "steps": e2e_steps,
                     "timer": "host wall clock around the synchronous host-buffer call"},
@@ -295,6 +299,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=-1, help="force a tile shape of the fused kernel (-1: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -17,7 +17,8 @@
  *    caller owns and keeps alive until the work on the stream has finished.
  *    The context owns only its workspace.
  *  - Work is asynchronous on the given stream (NULL = the context's own
- *    stream); synchronise that stream, or call stereo_sync(), before reading.
+ *    stream; cudaStreamLegacy and cudaStreamPerThread are accepted);
+ *    synchronise that stream, or call stereo_sync(), before reading.
  *  - Dmax counts disparities: d in [0, Dmax-1] (Sec. II). With downscaling,
  *    the processed image is (W/2) x (H/2) and D = ceil(Dmax/2) (Sec. I);
  *    processed-size maps (dl, dr, gcp) hold processed-resolution disparities,
@@ -115,8 +116,18 @@ STEREO_API int stereo_compute_host(stereo_ctx *ctx, const uint8_t *left_rgb, con
                                    int W, int H, int Dmax, float *disp_out, uint8_t *dl_out,
                                    uint8_t *dr_out, uint8_t *gcp_out);
 
-/* Blocks until all work on the context's own stream has finished. */
+/* Blocks until all work on the context's own stream has finished, then
+ * reports STEREO_ETIMEOUT if a bounded wait inside the fused kernel gave up
+ * during the last compute (the kernel then returned early and its maps are
+ * not valid). Work enqueued on a caller's stream must be synchronised by the
+ * caller first. */
 STEREO_API int stereo_sync(stereo_ctx *ctx);
+
+/* Polls each bounded wait of the fused kernel makes before it gives up, sets
+ * the error word and returns (default 2^22, far above any legitimate wait:
+ * the waits are between warps of one CTA and last one image row at most).
+ * 0 makes every wait give up at once, which exercises the error path. */
+STEREO_API int stereo_set_wait_limit(stereo_ctx *ctx, uint32_t polls);
 
 /* Copies intermediates of the last stereo_compute on this context into device
  * buffers (any may be NULL), enqueued on `stream` after that compute:
@@ -152,6 +163,23 @@ STEREO_API int stereo_stage_ms(stereo_ctx *ctx, float *ms, int n);
 
 /* Number of kernels (memsets excluded) the last stereo_compute launched. */
 STEREO_API int stereo_last_launch_count(const stereo_ctx *ctx);
+
+/* Tile shapes of the fused cost + aggregation + WTA kernel (columns per base
+ * x disparities per CTA, prefix width): 0: 104x4 16-bit, 1: 104x4 16-bit for
+ * wx up to 29, 2: 104x4 32-bit, 3: 104x4 32-bit for wx up to 29, 4: 64x4
+ * 16-bit, 5: 64x4 32-bit. 16-bit row prefixes need (2*wx+1) times the largest
+ * matching cost below 2^16. Every shape gives the same result; they differ
+ * only in speed. A compute with a shape that does not fit the parameters
+ * fails with EINVAL. */
+#define STEREO_NUM_TILES 6
+
+/* Fixes the tile shape used by later computes on this context (-1 = pick
+ * automatically from the frame shape and the SM count, the default).
+ * Returns EINVAL for an id outside [-1, STEREO_NUM_TILES-1]. */
+STEREO_API int stereo_set_tile(stereo_ctx *ctx, int tile);
+
+/* The tile shape a compute of this frame shape would use (>= 0), or EINVAL. */
+STEREO_API int stereo_get_tile(stereo_ctx *ctx, int W, int H, int Dmax);
 
 #ifdef __cplusplus
 }

@@ -58,6 +58,9 @@ _SIGNATURES = {
     "stereo_set_profiling": (_i, [_ctxp, _i]),
     "stereo_stage_ms": (_i, [_ctxp, ctypes.POINTER(ctypes.c_float), _i]),
     "stereo_last_launch_count": (_i, [_ctxp]),
+    "stereo_set_tile": (_i, [_ctxp, _i]),
+    "stereo_get_tile": (_i, [_ctxp, _i, _i, _i]),
+    "stereo_set_wait_limit": (_i, [_ctxp, ctypes.c_uint32]),
 }
 
 _lib = None
@@ -153,3 +156,21 @@ def stereo_stage_ms(ctx, n=NUM_STAGES):
 
 def stereo_last_launch_count(ctx):
     return load().stereo_last_launch_count(ctx)
+
+
+NUM_TILES = 6
+
+
+def stereo_set_tile(ctx, tile):
+    return check(ctx, load().stereo_set_tile(ctx, tile))
+
+
+def stereo_set_wait_limit(ctx, polls):
+    return check(ctx, load().stereo_set_wait_limit(ctx, polls))
+
+
+def stereo_get_tile(ctx, W, H, dmax):
+    rc = load().stereo_get_tile(ctx, W, H, dmax)
+    if rc < 0:
+        check(ctx, rc)
+    return rc

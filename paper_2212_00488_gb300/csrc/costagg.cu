@@ -4,8 +4,8 @@
 // The paper (Steps 3 and 5 of Sec. IV) writes the x-aggregated volume CA_x to
 // global memory and reads it back for the y pass. Here nothing of the volume
 // leaves the SM: each CTA sweeps its tile top to bottom and keeps, per
-// (column, disparity), a ring of 64 running vertical prefix sums in shared
-// memory.
+// (column, disparity, base), a ring of 64 running vertical prefix sums in
+// shared memory.
 //
 // Tile: one CTA owns a strip of XS columns for each base and a slab of DS
 // disparities [d0, d0+DS).
@@ -15,187 +15,344 @@
 //    C^R(x, y, d) = C^L(x+d, y, d), and for d in the slab the right windows
 //    land inside [x0-wx, x0+XS+DS-1+wx), next to the left windows.
 //
-// Per input row y and disparity d (phase A, one warp per (row, d)):
-//    S[i] = sum_{j<i} C^L(x0 - wx + j, y, d)     (row prefix, exact uint32)
-// where C^L is P when the match pixel x-d or the pixel itself is outside
-// the image. Each lane sums four consecutive costs, then a warp scan adds the
-// lanes' totals.
-// Per pixel (phase B, one thread per (base, column, 3 disparities)):
-//    CA_x = S[hi] - S[lo] over the pixel's own left/right arms   (Eq. 7)
-//    V(y+1) = V(y) + CA_x   -> ring slot (y+1) mod 64
-//    CA(yo) = V(yo + down + 1) - V(yo - up), yo = y - wy         (Eq. 8)
-//    key = min over d of (CA << 8 | d)                            (Eq. 9)
-// The min over slabs is an atomicMin on a 32-bit key per pixel and base. The
-// packed key keeps the smallest d among equal costs, the tie rule of Step 5.
+// Warp roles (the row buffers between them form a ring of RS slots guarded
+// by full/empty mbarriers):
+//  * Producer warp p (one per disparity d = d0 + p), for each input row y:
+//      S[i] = sum_{j<i} C^L(x0 - wx + j, y, d)      (row prefix, exact uint32)
+//    with C^L = P when the pixel or its match x - d is outside the image.
+//    Each lane sums KE consecutive costs, a warp scan adds the lanes' totals.
+//    The producers also stage the arm rows the consumers need.
+//  * Consumer thread (base, column, disparity), for each row:
+//      CA_x = S[hi] - S[lo] over the pixel's own left/right arms   (Eq. 7)
+//      V(y+1) = V(y) + CA_x  -> ring slot (y+1) mod 64
+//      CA(yo) = V(yo + down + 1) - V(yo - up), yo = y - wy        (Eq. 8)
+//      key = min over d of (CA << 8 | d)                           (Eq. 9)
+//    The DS disparities of a column sit in adjacent lanes, so the slab's
+//    minimum is a few shuffles; the minimum over slabs is one atomicMin per
+//    pixel and base. The packed key keeps the smallest d among equal costs,
+//    the tie rule of Step 5.
 // All sums are modular uint32: differences are exact because every window sum
 // is below 2^24 (checked on the host).
+//
+// Every wait on an mbarrier is bounded: after a.wait_limit polls the thread
+// sets a.err and returns, so a broken hand-off ends the kernel with an error
+// status instead of hanging the GPU.
 #include "internal.cuh"
+
+#include <type_traits>
 
 namespace stereo {
 namespace {
 
-constexpr int XS = 64;              // columns per base per CTA
-constexpr int DS = 6;               // disparities per CTA
-constexpr int NG = 2;               // disparity groups per (base, column)
-constexpr int DPT = DS / NG;        // disparities per thread
-constexpr int RB = 4;               // rows per phase A / phase B round
-constexpr int NT = 2 * XS * NG;     // 256 threads
-constexpr int NW = NT / 32;
-constexpr int KE = 4;               // prefix entries per lane in phase A
-constexpr int SWP = 176;            // S row pitch in words (== 16 mod 32)
-constexpr int SX_OFF = 3;           // S[i] at word SX_OFF + i: S[1 + 4 lane] is 16-byte aligned
-constexpr int LUT_N = 256 * 8;
-constexpr int RING_J = NG * XS;                 // words between disparities of a ring row
-constexpr int RING_SLOT = DPT * RING_J;         // words per ring slot
-constexpr int RING_BASE = kRing * RING_SLOT;    // words per base
-constexpr int SMEM_WORDS = LUT_N + RB * DS * SWP + 2 * RING_BASE;
-
-static_assert(32 * KE + SX_OFF + 1 <= SWP, "S row too short");
-static_assert(SWP % 32 == 16, "S pitch chosen so the two disparity groups use different banks");
-static_assert(NW == 8 && XS == 64, "warp -> (base, 16-column group) mapping assumes 8 warps");
-
-__global__ void __launch_bounds__(NT, 1) costagg_wta_kernel(const CostAggArgs a)
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *lut = smem;
-    uint32_t *sx = lut + LUT_N;
-    uint32_t *ring = sx + RB * DS * SWP;
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with the given parity to complete,
+// warp-uniform: the warp goes on only if every lane saw the phase complete.
+// On a timeout the error word is set and false is returned to every lane.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, uint32_t limit, uint32_t *err)
+{
+    bool ok = false;
+    for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, parity);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(err, 1u);
+    return ok;
+}
+
+template <int XS_, int DS_, int KE_, int RS_, bool S16_>
+struct Tile {
+    static constexpr int XS = XS_;            // columns per base
+    static constexpr int DS = DS_;            // disparities per CTA (divides 32)
+    static constexpr int KE = KE_;            // prefix entries per producer lane (odd)
+    static constexpr int RS = RS_;            // row slots between producers and consumers
+    static constexpr bool S16 = S16_;         // row prefixes kept mod 2^16 (window sums < 2^16)
+    using SType = typename std::conditional<S16_, uint16_t, uint32_t>::type;
+    static constexpr int LPX = 32 / DS;       // columns per consumer warp
+    static constexpr int NC = 2 * XS * DS;    // consumer threads
+    static constexpr int NPW = 4;             // producer warps; warp p fills rows y = p (mod 4)
+    static constexpr int NP = 32 * NPW;
+    static constexpr int NT = NC + NP;
+    static constexpr int NE = 32 * KE;        // S[0..NE]
+    // S row pitch in elements: a consumer warp's DS rows start LPX words apart
+    // modulo 32 banks, so its lanes' reads fall in distinct banks
+    static constexpr int SWP = NE + (S16 ? 2 * LPX : LPX);
+    static constexpr int B_BAR = 2 * RS * 8;
+    static constexpr int B_RING = kRing * NC * 4;
+    static constexpr int B_SX = RS * DS * SWP * (int)sizeof(SType);
+    static constexpr int B_LUT = 264 * 2;
+    static constexpr int BYTES = B_BAR + B_RING + B_SX + B_LUT;
+    static_assert(32 % DS == 0 && XS % LPX == 0, "a consumer warp holds whole columns");
+    static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
+    static_assert(NC % 32 == 0 && NT <= 1024, "");
+    static_assert(RS >= NPW, "every producer warp needs a slot of its own");
+    static_assert(BYTES <= 232448, "tile exceeds shared memory");
+};
+
+template <class T>
+__global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs a)
+{
+    using SType = typename T::SType;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + T::RS;
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smem + T::B_BAR);
+    SType *sx = reinterpret_cast<SType *>(ring + kRing * T::NC);               // [RS][DS][SWP]
+    uint16_t *lut_ad = reinterpret_cast<uint16_t *>(sx + T::RS * T::DS * T::SWP);   // [256]
+    uint16_t *lut_mc = lut_ad + 256;                                              // [8]
+
+    const int t = threadIdx.x, lane = t & 31;
     const int X = a.X, Y = a.Y, D = a.D, wx = a.wx, wy = a.wy;
-    const int x0 = blockIdx.x * XS;
-    const int d0 = blockIdx.y * DS;
-    const uint32_t P = a.P;
+    const int x0 = blockIdx.x * T::XS;
+    const int d0 = blockIdx.y * T::DS;
+    const uint32_t limit = a.wait_limit;
 
-    for (int i = tid; i < LUT_N; i += NT) lut[i] = a.lut[i];
-
-    // Phase B identity: warps 0-3 left base, 4-7 right base; a warp covers 16
-    // columns and both disparity groups (lane bit 4).
-    const int b = warp >> 2;
-    const int xl = ((warp & 3) << 4) + (lane & 15);
-    const int g = lane >> 4;
-    const int col = b == 0 ? x0 + xl : x0 - d0 + xl;
-    const bool valid = col >= 0 && col < X;
-    const uint32_t *arm = b ? a.arm_r : a.arm_l;
-    uint32_t *key = b ? a.key_r : a.key_l;
-    // The two groups of a warp sit XS words apart; xor-ing bit 4 of the column
-    // for group 1 puts the 32 lanes of a ring access in 32 different banks.
-    uint32_t *myring = ring + b * RING_BASE + g * XS + (xl ^ (g << 4));
-
-    uint32_t V[DPT];
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-        V[j] = 0;
-        myring[j * RING_J] = 0;          // slot 0 holds V(0) = 0
+    for (int i = t; i < 256; i += T::NT) lut_ad[i] = (uint16_t)a.lut_ad[i];
+    if (t < 8) lut_mc[t] = (uint16_t)a.lut_mc[t];   // index 7 never occurs
+    if (t == 0) {
+        for (int s = 0; s < T::RS; ++s) {
+            mbar_init(&full[s], 32);                // the producing warp
+            mbar_init(&empty[s], T::NC);            // every consumer
+        }
     }
     __syncthreads();
 
-    const int NE = XS + DS - 1 + 2 * wx;   // S[0..NE]
-
-    for (int yb = 0; yb < Y + wy; yb += RB) {
-        // ---------------- phase A: cost + row prefix for RB rows x DS disparities
-        for (int u = warp; u < RB * DS; u += NW) {
-            const int r = u / DS, dd = u - r * DS;
-            const int y = yb + r, d = d0 + dd;
-            if (y >= Y || d >= D) continue;                  // warp-uniform
+    if (t >= T::NC) {
+        // ======================= producers: warp pw fills rows pw, pw+4, ...
+        const int pw = (t - T::NC) >> 5;
+        const uint32_t P = a.P;
+        const int xb = x0 - wx + lane * T::KE;      // x of this lane's first entry
+        for (int y = pw; y < Y; y += T::NPW) {
+            const int s = y % T::RS;
+            // loads first: they overlap the wait for the slot
             const uint32_t *pl = a.pix_l + (size_t)y * X;
             const uint32_t *pr = a.pix_r + (size_t)y * X;
-            uint32_t c[KE];
-            uint32_t run = 0;
+            uint32_t pv[T::KE], qv[T::KE + T::DS - 1];
 #pragma unroll
-            for (int k = 0; k < KE; ++k) {
-                const int i = lane * KE + k;
-                const int xL = x0 - wx + i;
-                uint32_t v = 0;
-                if (i < NE) {
-                    if (xL >= d && xL < X) {
-                        const uint32_t p = __ldg(pl + xL), q = __ldg(pr + xL - d);
-                        const int ad = abs((int)(p & 0xFF) - (int)(q & 0xFF));
-                        const int hd = __popc((p ^ q) >> 8);
-                        v = lut[ad * 8 + hd];
-                    } else {
-                        v = P;
-                    }
+            for (int k = 0; k < T::KE; ++k) pv[k] = __ldg(pl + min(max(xb + k, 0), X - 1));
+#pragma unroll
+            for (int k = 0; k < T::KE + T::DS - 1; ++k)
+                qv[k] = __ldg(pr + min(max(xb + k - d0 - (T::DS - 1), 0), X - 1));
+            if (y >= T::RS && !mbar_wait_warp(&empty[s], ((y / T::RS) - 1) & 1, limit, a.err)) return;
+            uint32_t c[T::DS][T::KE];
+            uint32_t run[T::DS];
+#pragma unroll
+            for (int q = 0; q < T::DS; ++q) run[q] = 0;
+#pragma unroll
+            for (int k = 0; k < T::KE; ++k) {
+                const int xL = xb + k;
+                const uint32_t pw_ = pv[k];
+#pragma unroll
+                for (int q = 0; q < T::DS; ++q) {
+                    // match of xL at disparity d0 + q is x = xL - d0 - q: qv index k + DS-1 - q
+                    const uint32_t qw = qv[k + T::DS - 1 - q];
+                    const int ad = abs((int)(pw_ & 0xFF) - (int)(qw & 0xFF));
+                    const uint32_t v = (uint32_t)lut_ad[ad] + lut_mc[__popc((pw_ ^ qw) >> 8)];
+                    run[q] += (xL >= d0 + q && xL < X) ? v : P;
+                    c[q][k] = run[q];
                 }
-                run += v;
-                c[k] = run;
             }
-            uint32_t incl = run;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
+            for (int q = 0; q < T::DS; ++q) {
+                uint32_t incl = run[q];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                const uint32_t excl = incl - run[q];
+                SType *row = sx + (s * T::DS + q) * T::SWP;
+#pragma unroll
+                for (int k = 0; k < T::KE; ++k) row[1 + lane * T::KE + k] = (SType)(excl + c[q][k]);
+                if (lane == 0) row[0] = 0;
             }
-            const uint32_t excl = incl - run;
-            uint32_t *row = sx + (r * DS + dd) * SWP + SX_OFF;
-            *reinterpret_cast<uint4 *>(row + 1 + lane * KE) =
-                make_uint4(excl + c[0], excl + c[1], excl + c[2], excl + c[3]);
-            if (lane == 0) row[0] = 0;
+            mbar_arrive(&full[s]);
         }
-        __syncthreads();
-
-        // ---------------- phase B: arm differences, vertical ring, WTA
-#pragma unroll 1
-        for (int r = 0; r < RB; ++r) {
-            const int y = yb + r;
-            if (y < Y) {
-                const uint32_t am = valid ? __ldg(arm + (size_t)y * X + col) : 0u;
-                const int hm = am & 0xFF, hp = (am >> 8) & 0xFF;
-                const int slot = (y + 1) & (kRing - 1);
-#pragma unroll
-                for (int j = 0; j < DPT; ++j) {
-                    const int dd = g * DPT + j;
-                    const int base = xl + (b ? dd : 0) + wx;
-                    const uint32_t *row = sx + (r * DS + dd) * SWP + SX_OFF;
-                    V[j] += row[base + hp + 1] - row[base - hm];
-                    myring[slot * RING_SLOT + j * RING_J] = V[j];
-                }
-            }
-            const int yo = y - wy;
-            if (yo >= 0 && yo < Y) {
-                const uint32_t am = valid ? __ldg(arm + (size_t)yo * X + col) : 0u;
-                const int vm = (am >> 16) & 0xFF, vp = am >> 24;
-                const int shi = (yo + vp + 1) & (kRing - 1);
-                const int slo = (yo - vm) & (kRing - 1);
-                uint32_t best = 0xFFFFFFFFu;
-#pragma unroll
-                for (int j = 0; j < DPT; ++j) {
-                    const int d = d0 + g * DPT + j;
-                    const uint32_t ca = myring[shi * RING_SLOT + j * RING_J] - myring[slo * RING_SLOT + j * RING_J];
-                    if (d < D) best = min(best, (ca << 8) | (uint32_t)d);
-                }
-                best = min(best, __shfl_xor_sync(0xffffffffu, best, 16));
-                if (g == 0 && valid) atomicMin(key + (size_t)yo * X + col, best);
-            }
-        }
-        __syncthreads();
+        return;
     }
+
+    // =========================== consumers
+    const int wc = t >> 5;
+    const int j = lane & (T::DS - 1);             // disparity index in the slab
+    const int xi = lane / T::DS;
+    constexpr int XG = T::XS / T::LPX;            // consumer warps per base
+    const int b = wc >= XG;
+    const int x = (wc - b * XG) * T::LPX + xi;
+    const int col = b ? x0 - d0 + x : x0 + x;
+    const bool valid = col >= 0 && col < X;
+    const int colc = min(max(col, 0), X - 1);
+    const int d = d0 + j;
+    const uint32_t dkey = d < D ? (uint32_t)d : 0xFFFFFFFFu;
+    uint32_t *key = b ? a.key_r : a.key_l;
+    const uint32_t *arm = (b ? a.arm_r : a.arm_l) + colc;
+    uint32_t *myring = ring + t;
+    const int sbase = x + wx + (b ? j : 0);       // S index of this pixel's own column
+    const int rows = Y + wy;                      // row steps: inputs 0..Y-1, outputs lag by wy
+
+    // arm words of rows y (horizontal arms) and y - wy (vertical arms), three
+    // rows ahead in registers
+    uint32_t ah0, ah1, ah2, av0, av1, av2;
+    auto fetch = [&](int y, uint32_t &h, uint32_t &v) {
+        h = __ldg(arm + (size_t)min(y, Y - 1) * X);
+        v = __ldg(arm + (size_t)min(max(y - wy, 0), Y - 1) * X);
+    };
+    fetch(0, ah0, av0);
+    fetch(1, ah1, av1);
+
+    myring[0] = 0;                                // V(0) = 0
+    uint32_t V = 0;
+    auto step = [&](int y, uint32_t h, uint32_t v) -> bool {
+        const int s = y % T::RS;
+        const int yo = y - wy;
+        if (y < Y) {
+            if (!mbar_wait_warp(&full[s], (y / T::RS) & 1, limit, a.err)) return false;
+            const SType *row = sx + (s * T::DS + j) * T::SWP + sbase;
+            uint32_t cax = (uint32_t)row[((h >> 8) & 0xFF) + 1] - (uint32_t)row[-(int)(h & 0xFF)];
+            if (T::S16) cax &= 0xFFFFu;
+            V += cax;
+            myring[((y + 1) & (kRing - 1)) * T::NC] = V;
+            mbar_arrive(&empty[s]);
+        }
+        if (yo >= 0) {
+            const int up = (v >> 16) & 0xFF, down = v >> 24;
+            const uint32_t hi = myring[((yo + down + 1) & (kRing - 1)) * T::NC];
+            const uint32_t lo = myring[((yo - up) & (kRing - 1)) * T::NC];
+            uint32_t best = dkey == 0xFFFFFFFFu ? dkey : (((hi - lo) << 8) | dkey);
+#pragma unroll
+            for (int o = 1; o < T::DS; o <<= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (j == 0 && valid) atomicMin(key + (size_t)yo * X + col, best);
+        }
+        return true;
+    };
+    for (int y = 0; y < rows; y += 3) {
+        fetch(y + 2, ah2, av2);
+        if (!step(y, ah0, av0)) return;
+        if (y + 1 >= rows) break;
+        fetch(y + 3, ah0, av0);
+        if (!step(y + 1, ah1, av1)) return;
+        if (y + 2 >= rows) break;
+        fetch(y + 4, ah1, av1);
+        if (!step(y + 2, ah2, av2)) return;
+    }
+}
+
+// Tile shapes (XS x DS). One CTA per SM; the ring of 64 prefix rows per
+// (column, disparity, base) dominates shared memory.
+using T0 = Tile<104, 4, 5, 8, true>;    // wx <= 26, window sums < 2^16
+using T1 = Tile<104, 4, 7, 6, true>;    // wx <= 29, window sums < 2^16
+using T2 = Tile<104, 4, 5, 4, false>;   // wx <= 26, 32-bit prefixes
+using T3 = Tile<104, 4, 7, 4, false>;   // wx <= 29, 32-bit prefixes
+using T4 = Tile<64, 4, 5, 8, true>;     // narrow frames
+using T5 = Tile<64, 4, 7, 4, false>;
+
+template <class T>
+bool fits(const CostAggArgs &a)
+{
+    if (T::XS + T::DS - 1 + 2 * a.wx > T::NE) return false;
+    // 16-bit prefixes need every horizontal window sum below 2^16
+    return !T::S16 || (uint64_t)(2 * a.wx + 1) * a.P < 65536u;
+}
+
+template <class T>
+cudaError_t setup_one()
+{
+    return cudaFuncSetAttribute(costagg_wta_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::BYTES);
+}
+
+template <class T>
+void grid_of(const CostAggArgs &a, int &nstrip, int &nslab)
+{
+    nslab = (a.D + T::DS - 1) / T::DS;
+    const int dlast = (nslab - 1) * T::DS;
+    nstrip = (a.X + dlast + T::XS - 1) / T::XS;
+}
+
+template <class T>
+cudaError_t launch_one(const CostAggArgs &a, cudaStream_t s)
+{
+    int nstrip, nslab;
+    grid_of<T>(a, nstrip, nslab);
+    costagg_wta_kernel<T><<<dim3(nstrip, nslab), T::NT, T::BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
+double estimate(const CostAggArgs &a, int nsm)
+{
+    // time ~ waves x per-CTA work per row (producer entries + consumer cells)
+    int nstrip, nslab;
+    grid_of<T>(a, nstrip, nslab);
+    const long ctas = (long)nstrip * nslab;
+    const long waves = (ctas + nsm - 1) / nsm;
+    const double work = (double)T::DS * (T::XS + T::DS + 2 * a.wx) + 2.0 * T::XS * T::DS;
+    return (double)waves * work * (T::S16 ? 1.0 : 1.05);
 }
 
 }  // namespace
 
-size_t costagg_smem_bytes(int wx)
-{
-    if (wx < 0 || XS + DS - 1 + 2 * wx > 32 * KE) return 0;
-    return (size_t)SMEM_WORDS * 4;
-}
-
 cudaError_t costagg_setup()
 {
-    return cudaFuncSetAttribute(costagg_wta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                SMEM_WORDS * 4);
+    cudaError_t e;
+    if ((e = setup_one<T0>()) != cudaSuccess) return e;
+    if ((e = setup_one<T1>()) != cudaSuccess) return e;
+    if ((e = setup_one<T2>()) != cudaSuccess) return e;
+    if ((e = setup_one<T3>()) != cudaSuccess) return e;
+    if ((e = setup_one<T4>()) != cudaSuccess) return e;
+    return setup_one<T5>();
+}
+
+int costagg_pick(const CostAggArgs &a, int nsm)
+{
+    int best = -1;
+    double bt = 0;
+    auto consider = [&](int id, bool ok, double est) {
+        if (ok && (best < 0 || est < bt)) { best = id; bt = est; }
+    };
+    consider(0, fits<T0>(a), estimate<T0>(a, nsm));
+    consider(1, fits<T1>(a), estimate<T1>(a, nsm) * 1.01);
+    consider(2, fits<T2>(a), estimate<T2>(a, nsm));
+    consider(3, fits<T3>(a), estimate<T3>(a, nsm) * 1.01);
+    consider(4, fits<T4>(a), estimate<T4>(a, nsm));
+    consider(5, fits<T5>(a), estimate<T5>(a, nsm) * 1.01);
+    return best;
 }
 
 cudaError_t launch_costagg(const CostAggArgs &a, cudaStream_t s)
 {
-    size_t smem = costagg_smem_bytes(a.wx);
-    if (smem == 0 || a.wy > kMaxWy || a.wy < 0) return cudaErrorInvalidValue;
-    const int nslab = (a.D + DS - 1) / DS;
-    const int dlast = (nslab - 1) * DS;
-    const int nstrip = (a.X + dlast + XS - 1) / XS;
-    dim3 grid(nstrip, nslab);
-    costagg_wta_kernel<<<grid, NT, smem, s>>>(a);
-    return cudaGetLastError();
+    if (a.wy > kMaxWy || a.wy < 0 || a.wx < 0 || a.wx > kMaxWx) return cudaErrorInvalidValue;
+    const int tile = a.tile >= 0 ? a.tile : costagg_pick(a, a.num_sms);
+    switch (tile) {
+    case 0: return fits<T0>(a) ? launch_one<T0>(a, s) : cudaErrorInvalidValue;
+    case 1: return fits<T1>(a) ? launch_one<T1>(a, s) : cudaErrorInvalidValue;
+    case 2: return fits<T2>(a) ? launch_one<T2>(a, s) : cudaErrorInvalidValue;
+    case 3: return fits<T3>(a) ? launch_one<T3>(a, s) : cudaErrorInvalidValue;
+    case 4: return fits<T4>(a) ? launch_one<T4>(a, s) : cudaErrorInvalidValue;
+    case 5: return fits<T5>(a) ? launch_one<T5>(a, s) : cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace stereo

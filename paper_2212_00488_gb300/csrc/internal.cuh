@@ -24,21 +24,31 @@ struct CostAggArgs {
     const uint32_t *pix_l, *pix_r;   // [Y][X]
     const uint32_t *arm_l, *arm_r;   // [Y][X]
     uint32_t *key_l, *key_r;         // [Y][X] min over d of (CA << 8 | d); preset to ~0
-    const uint32_t *lut;             // [256 * 8] combined cost table, index ad * 8 + hamming
+    const uint32_t *lut_ad;          // [256] quantised AD cost (Eq. 4) by |grey difference|
+    const uint32_t *lut_mc;          // [8] quantised census cost (Eq. 5) by Hamming distance
+    uint32_t *err;                   // set to nonzero when a bounded wait gives up
+    uint32_t wait_limit;             // polls per mbarrier wait before giving up
     int X, Y, D;
     int wx, wy;
     uint32_t P;                      // cost of a match outside the image
+    int tile;                        // tile shape id, -1 = pick from the shape
+    int num_sms;                     // SMs of the device (for the pick)
 };
+
+// Number of tile shapes of the fused kernel (ids 0 .. kNumTiles-1).
+constexpr int kNumTiles = 6;
+int costagg_pick(const CostAggArgs &a, int nsm);
 
 // Launchers (each returns the launch error, cudaSuccess on success).
 cudaError_t launch_grey(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t *g_l, uint8_t *g_r,
                         int W, int H, cudaStream_t s);
 cudaError_t launch_downscale(const uint8_t *g_l, const uint8_t *g_r, uint8_t *s_l, uint8_t *s_r,
                              int W, int H, cudaStream_t s);
-// Also presets the WTA keys of both bases to ~0 for the fused kernel.
+// Also presets the WTA keys of both bases to ~0 and clears the fused
+// kernel's error word for this frame.
 cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix_l, uint32_t *pix_r,
                            uint32_t *arm_l, uint32_t *arm_r, uint32_t *key_l, uint32_t *key_r,
-                           int X, int Y, int wx, int wy, int tc, cudaStream_t s);
+                           uint32_t *err, int X, int Y, int wx, int wy, int tc, cudaStream_t s);
 cudaError_t launch_costagg(const CostAggArgs &a, cudaStream_t s);
 cudaError_t launch_refine(const uint32_t *key_l, const uint32_t *key_r, const uint8_t *grey_l,
                           int X, int Y, int T, uint8_t *dl, uint8_t *dr, uint8_t *gcp, uint8_t *dm,
@@ -48,8 +58,6 @@ cudaError_t launch_upscale(const float *dplus, const uint8_t *grey_low, const ui
 cudaError_t launch_unpack_planes(const uint32_t *pix, const uint32_t *arm, uint8_t *grey,
                                  uint8_t *census, uint32_t *arms, int X, int Y, cudaStream_t s);
 
-// Shared-memory bytes the fused kernel needs for wx (0 if unsupported).
-size_t costagg_smem_bytes(int wx);
 
 // One-time per-device function attributes (large dynamic shared memory);
 // call with the device current.

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kSupNT) support_kernel(
     const uint8_t *__restrict__ g_l, const uint8_t *__restrict__ g_r,
     uint32_t *__restrict__ pix_l, uint32_t *__restrict__ pix_r,
     uint32_t *__restrict__ arm_l, uint32_t *__restrict__ arm_r,
-    uint32_t *__restrict__ key_l, uint32_t *__restrict__ key_r,
+    uint32_t *__restrict__ key_l, uint32_t *__restrict__ key_r, uint32_t *__restrict__ err,
     int X, int Y, int wx, int wy, int tc)
 {
     extern __shared__ uint8_t tile[];
@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kSupNT) support_kernel(
     const int hx = max(wx, 2), hy = max(wy, 1);
     const int TW = kSupTX + 2 * hx, TH = kSupTY + 2 * hy;
     const int x0 = blockIdx.x * kSupTX, y0 = blockIdx.y * kSupTY;
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *err = 0u;
 
     for (int i = threadIdx.x; i < TW * TH; i += kSupNT) {
         int ty = i / TW, tx = i - ty * TW;
@@ -159,13 +160,13 @@ cudaError_t launch_downscale(const uint8_t *g_l, const uint8_t *g_r, uint8_t *s_
 
 cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix_l, uint32_t *pix_r,
                            uint32_t *arm_l, uint32_t *arm_r, uint32_t *key_l, uint32_t *key_r,
-                           int X, int Y, int wx, int wy, int tc, cudaStream_t s)
+                           uint32_t *err, int X, int Y, int wx, int wy, int tc, cudaStream_t s)
 {
     const int hx = wx > 2 ? wx : 2, hy = wy > 1 ? wy : 1;
     size_t smem = (size_t)(kSupTX + 2 * hx) * (kSupTY + 2 * hy);
     dim3 grid((X + kSupTX - 1) / kSupTX, (Y + kSupTY - 1) / kSupTY, 2);
-    support_kernel<<<grid, kSupNT, smem, s>>>(g_l, g_r, pix_l, pix_r, arm_l, arm_r, key_l, key_r, X, Y, wx,
-                                               wy, tc);
+    support_kernel<<<grid, kSupNT, smem, s>>>(g_l, g_r, pix_l, pix_r, arm_l, arm_r, key_l, key_r, err, X, Y,
+                                               wx, wy, tc);
     return cudaGetLastError();
 }
 

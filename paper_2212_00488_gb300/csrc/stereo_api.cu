@@ -19,9 +19,12 @@ struct stereo_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
 
-    uint32_t lut_host[256 * 8];
+    uint32_t lut_host[256 + 8];     // quantised AD costs [256], then census costs [8]
     uint32_t P = 0;
     uint32_t *d_lut = nullptr;
+    uint32_t *d_err = nullptr;      // device error word of the fused kernel's bounded waits
+    uint32_t *h_err = nullptr;      // pinned host copy
+    uint32_t wait_limit = 1u << 22;
 
     void *ws = nullptr;
     size_t ws_size = 0;
@@ -46,6 +49,8 @@ struct stereo_ctx {
     float *out_disp = nullptr, *dplus = nullptr;
     uint8_t *out_dl = nullptr, *out_dr = nullptr, *out_gcp = nullptr;
     int launches = 0;
+    int tile = -1;          // fused-kernel tile shape, -1 = automatic
+    int num_sms = 0;
 
     // Profiling: a ring of event sets, one per recent frame, harvested when a
     // slot is reused (by then its frame has long finished), so timing adds no
@@ -100,18 +105,17 @@ int cuda_fail(stereo_ctx *c, cudaError_t e, const char *what)
 
 // Eqs. 4-5 on intensities scaled to [0, 1], quantised to round(scale * v),
 // half away from zero, evaluated in double on the host; the device only reads
-// the table. Index ad * 8 + hamming; hamming 7 never occurs.
+// the tables. AD by |grey difference| (0..255), census by Hamming distance
+// (0..6; entry 7 never occurs).
 void build_lut(stereo_ctx *c)
 {
     const double s = c->p.cost_scale;
-    uint32_t ad[256], mc[8];
+    uint32_t *ad = c->lut_host, *mc = c->lut_host + 256;
     for (int a = 0; a < 256; ++a)
         ad[a] = (uint32_t)std::llround(s * (1.0 - std::exp(-((double)a / 255.0) / c->p.lambda_ad)));
     for (int h = 0; h <= 6; ++h)
         mc[h] = (uint32_t)std::llround(s * (1.0 - std::exp(-(double)h / c->p.lambda_mc)));
     mc[7] = mc[6];
-    for (int a = 0; a < 256; ++a)
-        for (int h = 0; h < 8; ++h) c->lut_host[a * 8 + h] = ad[a] + mc[h];
     c->P = ad[255] + mc[6];
 }
 
@@ -124,6 +128,9 @@ int check_params(stereo_ctx *c, const stereo_params &p)
     if (p.t_fill < 0 || p.t_fill > 255) return fail(c, STEREO_EINVAL, "t_fill must be in [0, 255]");
     if (p.downscale != 0 && p.downscale != 1) return fail(c, STEREO_EINVAL, "downscale must be 0 or 1");
     if (p.cost_scale < 1 || p.cost_scale > (1 << 20)) return fail(c, STEREO_EINVAL, "cost_scale must be in [1, 2^20]");
+    // the fused kernel keeps the cost table in 16 bits
+    if (p.cost_scale * ((1.0 - std::exp(-1.0 / p.lambda_ad)) + (1.0 - std::exp(-6.0 / p.lambda_mc))) + 1.0 > 65535.0)
+        return fail(c, STEREO_EINVAL, "cost_scale %d too large: a matching cost must stay below 2^16", p.cost_scale);
     // the packed WTA key holds the aggregated cost in 24 bits
     const double pmax = p.cost_scale * ((1.0 - std::exp(-1.0 / p.lambda_ad)) + (1.0 - std::exp(-6.0 / p.lambda_mc))) + 1.0;
     const double worst = (double)(2 * p.wx + 1) * (2 * p.wy + 1) * pmax;
@@ -225,7 +232,7 @@ cudaError_t run_stage(stereo_ctx *c, int stage, cudaStream_t s)
     case STEREO_STAGE_SUPPORT:
         c->launches++;
         return launch_support(c->gs[0], c->gs[1], c->pix[0], c->pix[1], c->arm[0], c->arm[1], c->key[0],
-                              c->key[1], c->X, c->Y, c->p.wx, c->p.wy, c->p.tc, s);
+                              c->key[1], c->d_err, c->X, c->Y, c->p.wx, c->p.wy, c->p.tc, s);
     case STEREO_STAGE_COSTAGG: {
         CostAggArgs a;
         a.pix_l = c->pix[0];
@@ -234,13 +241,18 @@ cudaError_t run_stage(stereo_ctx *c, int stage, cudaStream_t s)
         a.arm_r = c->arm[1];
         a.key_l = c->key[0];
         a.key_r = c->key[1];
-        a.lut = c->d_lut;
+        a.lut_ad = c->d_lut;
+        a.lut_mc = c->d_lut + 256;
+        a.err = c->d_err;
+        a.wait_limit = c->wait_limit;
         a.X = c->X;
         a.Y = c->Y;
         a.D = c->D;
         a.wx = c->p.wx;
         a.wy = c->p.wy;
         a.P = c->P;
+        a.tile = c->tile;
+        a.num_sms = c->num_sms;
         c->launches++;
         return launch_costagg(a, s);
     }
@@ -337,12 +349,16 @@ int stereo_create(stereo_ctx **out, int device, const stereo_params *p, size_t m
     }
     c->device = device;
     c->mem_cap = mem_cap_bytes;
+    c->num_sms = prop.multiProcessorCount;
     DeviceGuard g(device);
     build_lut(c);
     if ((e = costagg_setup()) != cudaSuccess || (e = refine_setup()) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_lut, sizeof c->lut_host)) != cudaSuccess ||
-        (e = cudaMemcpy(c->d_lut, c->lut_host, sizeof c->lut_host, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(c->d_lut, c->lut_host, sizeof c->lut_host, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_err, sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset(c->d_err, 0, sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaHostAlloc(&c->h_err, sizeof(uint32_t), cudaHostAllocDefault)) != cudaSuccess) {
         cudaGetLastError();
         stereo_destroy(c);
         return STEREO_ECUDA;
@@ -362,6 +378,8 @@ void stereo_destroy(stereo_ctx *c)
                 if (ev) cudaEventDestroy(ev);
         if (c->ws) cudaFree(c->ws);
         if (c->d_lut) cudaFree(c->d_lut);
+        if (c->d_err) cudaFree(c->d_err);
+        if (c->h_err) cudaFreeHost(c->h_err);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -428,7 +446,10 @@ int stereo_compute_host(stereo_ctx *c, const uint8_t *left_rgb, const uint8_t *r
         return cuda_fail(c, e, "device-to-host copy");
     if (gcp_out && (e = cudaMemcpyAsync(gcp_out, c->stage_maps + 2 * nl, nl, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(c, e, "device-to-host copy");
+    if ((e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(c, e, "device-to-host copy");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    if (*c->h_err) return fail(c, STEREO_ETIMEOUT, "a bounded wait in the fused kernel gave up");
     return STEREO_OK;
 }
 
@@ -437,7 +458,18 @@ int stereo_sync(stereo_ctx *c)
     if (!c) return STEREO_EINVAL;
     DeviceGuard g(c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? STEREO_OK : cuda_fail(c, e, "stream synchronize");
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    if ((e = cudaMemcpy(c->h_err, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(c, e, "device-to-host copy");
+    if (*c->h_err) return fail(c, STEREO_ETIMEOUT, "a bounded wait in the fused kernel gave up");
+    return STEREO_OK;
+}
+
+int stereo_set_wait_limit(stereo_ctx *c, uint32_t polls)
+{
+    if (!c) return STEREO_EINVAL;
+    c->wait_limit = polls;
+    return STEREO_OK;
 }
 
 int stereo_debug_planes(stereo_ctx *c, uint8_t *grey_l, uint8_t *grey_r, uint8_t *census_l, uint8_t *census_r,
@@ -505,6 +537,27 @@ int stereo_stage_ms(stereo_ctx *c, float *ms, int n)
 int stereo_last_launch_count(const stereo_ctx *c)
 {
     return c ? c->launches : 0;
+}
+
+int stereo_set_tile(stereo_ctx *c, int tile)
+{
+    if (!c) return STEREO_EINVAL;
+    if (tile < -1 || tile >= kNumTiles) return fail(c, STEREO_EINVAL, "tile %d out of range [-1, %d]", tile, kNumTiles - 1);
+    c->tile = tile;
+    return STEREO_OK;
+}
+
+int stereo_get_tile(stereo_ctx *c, int W, int H, int Dmax)
+{
+    if (!c || W < 1 || H < 1 || Dmax < 1) return STEREO_EINVAL;
+    if (c->tile >= 0) return c->tile;
+    CostAggArgs a{};
+    a.X = c->p.downscale ? W / 2 : W;
+    a.Y = c->p.downscale ? H / 2 : H;
+    a.D = c->p.downscale ? (Dmax + 1) / 2 : Dmax;
+    a.wx = c->p.wx;
+    a.wy = c->p.wy;
+    return costagg_pick(a, c->num_sms);
 }
 
 }  // extern "C"

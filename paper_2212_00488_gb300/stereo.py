@@ -18,6 +18,18 @@ class StereoOutput:
     gcp: torch.Tensor | None = None
 
 
+CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the handle of the legacy default stream
+
+
+def stream_handle(s: torch.cuda.Stream) -> int:
+    """The cudaStream_t to pass to the C ABI for a torch stream.
+
+    torch's default stream has handle 0, which the ABI reads as "the context's
+    own stream"; it is passed as cudaStreamLegacy instead so the library's work
+    stays ordered with torch's."""
+    return s.cuda_stream if s.cuda_stream != 0 else CUDA_STREAM_LEGACY
+
+
 def processed_shape(W: int, H: int, dmax: int, downscale: bool):
     if downscale:
         return W // 2, H // 2, (dmax + 1) // 2
@@ -82,7 +94,7 @@ class Stereo:
         _lib.stereo_compute(self.ctx, left.data_ptr(), right.data_ptr(), W, H, dmax, out.disp.data_ptr(),
                             out.dl.data_ptr() if out.dl is not None else 0,
                             out.dr.data_ptr() if out.dr is not None else 0,
-                            out.gcp.data_ptr() if out.gcp is not None else 0, s.cuda_stream)
+                            out.gcp.data_ptr() if out.gcp is not None else 0, stream_handle(s))
         return out
 
     def debug_planes(self, X: int, Y: int, device=None):
@@ -97,7 +109,7 @@ class Stereo:
         _lib.stereo_debug_planes(self.ctx, t["grey_l"].data_ptr(), t["grey_r"].data_ptr(),
                                  t["census_l"].data_ptr(), t["census_r"].data_ptr(), t["arms_l"].data_ptr(),
                                  t["arms_r"].data_ptr(), t["dm"].data_ptr(), t["dplus"].data_ptr(),
-                                 s.cuda_stream)
+                                 stream_handle(s))
         return t
 
     def compute_host(self, left, right, dmax: int, disp, dl=None, dr=None, gcp=None):

@@ -31,10 +31,11 @@ def _params(**kw):
     return p
 
 
-def _run_gpu(left, right, dmax, p):
-    from paper_2212_00488_gb300 import Stereo
+def _run_gpu(left, right, dmax, p, tile=-1):
+    from paper_2212_00488_gb300 import Stereo, _lib
     st = Stereo(0, lambda_ad=p.lambda_ad, lambda_mc=p.lambda_mc, tc=p.tc, wx=p.wx, wy=p.wy,
                 t_fill=p.t_fill, downscale=p.downscale, cost_scale=p.cost_scale)
+    _lib.stereo_set_tile(st.ctx, tile)
     lt = torch.from_numpy(np.ascontiguousarray(left)).cuda()
     rt = torch.from_numpy(np.ascontiguousarray(right)).cuda()
     out = st(lt, rt, dmax, maps=True)
@@ -82,6 +83,15 @@ def test_paper_shape_full_pipeline():
     s = scenes.make_scene(1436, 992, 145, planes=40, seed=0)
     p = _params()
     _compare(_run_gpu(s.left, s.right, 145, p), oracle.pipeline(s.left, s.right, 145, p), "1436x992/145")
+
+
+@pytest.mark.parametrize("tile", range(6))
+def test_every_tile_shape(tile):
+    # each tile shape of the fused kernel gives the oracle's result, on a frame
+    # with ragged strips and slabs and both clipped image borders
+    s = scenes.make_scene(300, 150, 50, planes=6, seed=12)
+    p = _params(downscale=0)
+    _compare(_run_gpu(s.left, s.right, 50, p, tile=tile), oracle.pipeline(s.left, s.right, 50, p), f"tile {tile}")
 
 
 @pytest.mark.parametrize("W,H,dmax,ds", [
@@ -146,6 +156,7 @@ def test_host_entry_point_matches_device_entry_point():
 
 def test_stage_relaunch_and_profiling():
     from paper_2212_00488_gb300 import Stereo, _lib
+    from paper_2212_00488_gb300.stereo import stream_handle
     s = scenes.make_scene(300, 200, 40, planes=5, seed=6)
     st = Stereo(0)
     _lib.stereo_set_profiling(st.ctx, True)
@@ -158,7 +169,7 @@ def test_stage_relaunch_and_profiling():
     assert _lib.stereo_last_launch_count(st.ctx) == 6
     first = out.dl.clone()
     for stage in range(_lib.NUM_STAGES):
-        _lib.stereo_launch_stage(st.ctx, stage, torch.cuda.current_stream().cuda_stream)
+        _lib.stereo_launch_stage(st.ctx, stage, stream_handle(torch.cuda.current_stream()))
     torch.cuda.synchronize()
     assert torch.equal(first, out.dl)
     st.close()
@@ -187,3 +198,34 @@ def test_argument_errors():
         Stereo(0, wx=40)            # beyond the supported arm cap
     with pytest.raises(_lib.StereoError):
         Stereo(0, cost_scale=1 << 14)   # aggregated costs would overflow the 24-bit key
+    with pytest.raises(_lib.StereoError):
+        Stereo(0, wx=0, wy=0, cost_scale=40000)   # one cost would overflow the 16-bit table
+    st = Stereo(0)
+    with pytest.raises(_lib.StereoError):
+        _lib.stereo_set_tile(st.ctx, _lib.NUM_TILES)
+    assert 0 <= _lib.stereo_get_tile(st.ctx, 1436, 992, 145) < _lib.NUM_TILES
+    st.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers():
+    # the fused kernel's producer/consumer waits are bounded: with a limit of
+    # zero polls every wait gives up at once, the kernel returns early and the
+    # host sees ETIMEOUT; no GPU state is harmed and the next frame is correct
+    from paper_2212_00488_gb300 import Stereo, _lib
+    s = scenes.make_scene(200, 100, 30, planes=4, seed=2)
+    st = Stereo(0, downscale=0)
+    lt = torch.from_numpy(s.left).cuda()
+    rt = torch.from_numpy(s.right).cuda()
+    _lib.stereo_set_wait_limit(st.ctx, 0)
+    st(lt, rt, 30, maps=True)
+    torch.cuda.synchronize()
+    with pytest.raises(_lib.StereoError) as e:
+        _lib.stereo_sync(st.ctx)
+    assert e.value.code == _lib.STEREO_ETIMEOUT
+    _lib.stereo_set_wait_limit(st.ctx, 1 << 22)
+    out = st(lt, rt, 30, maps=True)
+    torch.cuda.synchronize()
+    _lib.stereo_sync(st.ctx)
+    ref = oracle.pipeline(s.left, s.right, 30, _params(downscale=0))
+    assert np.array_equal(out.dl.cpu().numpy(), ref.dl)
+    st.close()
