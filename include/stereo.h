@@ -124,9 +124,11 @@ STEREO_API int stereo_compute_host(stereo_ctx *ctx, const uint8_t *left_rgb, con
 STEREO_API int stereo_sync(stereo_ctx *ctx);
 
 /* Polls each bounded wait of the fused kernel makes before it gives up, sets
- * the error word and returns (default 2^22, far above any legitimate wait:
- * the waits are between warps of one CTA and last one image row at most).
- * 0 makes every wait give up at once, which exercises the error path. */
+ * the error word and returns. The waiting warp sleeps at most 256 ns between
+ * polls, so the default of 2^20 polls bounds a wait by about 0.3 s, far above
+ * any legitimate wait (the waits are between warps of one CTA and last one
+ * image row at most). 0 makes every wait give up at its first poll, which
+ * exercises the error path. */
 STEREO_API int stereo_set_wait_limit(stereo_ctx *ctx, uint32_t polls);
 
 /* Copies intermediates of the last stereo_compute on this context into device
@@ -165,12 +167,12 @@ STEREO_API int stereo_stage_ms(stereo_ctx *ctx, float *ms, int n);
 STEREO_API int stereo_last_launch_count(const stereo_ctx *ctx);
 
 /* Tile shapes of the fused cost + aggregation + WTA kernel (columns per base
- * x disparities per CTA, prefix width): 0: 104x4 16-bit, 1: 104x4 16-bit for
- * wx up to 29, 2: 104x4 32-bit, 3: 104x4 32-bit for wx up to 29, 4: 64x4
- * 16-bit, 5: 64x4 32-bit. 16-bit row prefixes need (2*wx+1) times the largest
- * matching cost below 2^16. Every shape gives the same result; they differ
- * only in speed. A compute with a shape that does not fit the parameters
- * fails with EINVAL. */
+ * x disparities per CTA, prefix width, disparities per consumer thread):
+ * 0: 104x4 16-bit 2, 1: 104x4 16-bit 2 for wx up to 29, 2: 104x4 32-bit 2,
+ * 3: 96x4 32-bit 2 for wx up to 29, 4: 96x4 16-bit 4, 5: 64x4 16-bit 2.
+ * 16-bit row prefixes need (2*wx+1) times the largest matching cost below
+ * 2^16. Every shape gives the same result; they differ only in speed. A
+ * compute with a shape that does not fit the parameters fails with EINVAL. */
 #define STEREO_NUM_TILES 6
 
 /* Fixes the tile shape used by later computes on this context (-1 = pick

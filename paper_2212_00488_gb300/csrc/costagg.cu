@@ -60,69 +60,93 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
                  : "memory");
 }
 
+// One poll of the phase with the given parity. A thread whose phase is not
+// complete is suspended until the phase completes or at most kSuspendNs have
+// passed, so waiting warps leave the issue slots to the warps doing the work.
+constexpr uint32_t kSuspendNs = 1000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
 
 // Bounded wait for the phase of `bar` with the given parity to complete,
 // warp-uniform: the warp goes on only if every lane saw the phase complete.
-// On a timeout the error word is set and false is returned to every lane.
+// After `limit` polls (each suspends at most kSuspendNs) the error word is set
+// and false is returned to every lane.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, uint32_t limit, uint32_t *err)
 {
     bool ok = false;
-    for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, parity);
+    for (uint32_t it = 0; !ok && it < limit; ++it) ok = mbar_try_wait(bar, parity);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok && (threadIdx.x & 31) == 0) atomicOr(err, 1u);
     return ok;
 }
 
-template <int XS_, int DS_, int KE_, int RS_, bool S16_>
+template <int XS_, int DS_, int KE_, int RS_, bool S16_, int DPT_, int NPW_>
 struct Tile {
     static constexpr int XS = XS_;            // columns per base
-    static constexpr int DS = DS_;            // disparities per CTA (divides 32)
+    static constexpr int DS = DS_;            // disparities per CTA
     static constexpr int KE = KE_;            // prefix entries per producer lane (odd)
     static constexpr int RS = RS_;            // row slots between producers and consumers
     static constexpr bool S16 = S16_;         // row prefixes kept mod 2^16 (window sums < 2^16)
+    static constexpr int DPT = DPT_;          // disparities per consumer thread
     using SType = typename std::conditional<S16_, uint16_t, uint32_t>::type;
-    static constexpr int LPX = 32 / DS;       // columns per consumer warp
-    static constexpr int NC = 2 * XS * DS;    // consumer threads
-    static constexpr int NPW = 4;             // producer warps; warp p fills rows y = p (mod 4)
+    static constexpr int G = DS / DPT;        // consumer threads per column (adjacent lanes)
+    static constexpr int LPX = 32 / G;        // columns per consumer warp
+    static constexpr int NCT = 2 * XS * G;    // consumer threads
+    static constexpr int NPW = NPW_;          // producer warps; warp p fills rows y = p (mod NPW)
     static constexpr int NP = 32 * NPW;
-    static constexpr int NT = NC + NP;
+    static constexpr int NT = NCT + NP;
     static constexpr int NE = 32 * KE;        // S[0..NE]
-    // S row pitch in elements: a consumer warp's DS rows start LPX words apart
-    // modulo 32 banks, so its lanes' reads fall in distinct banks
+    // S row pitch in elements: the G groups of a consumer warp read rows that
+    // start LPX words apart modulo the 32 banks
     static constexpr int SWP = NE + (S16 ? 2 * LPX : LPX);
     static constexpr int B_BAR = 2 * RS * 8;
-    static constexpr int B_RING = kRing * NC * 4;
+    static constexpr int B_RING = kRing * NCT * DPT * 4;
     static constexpr int B_SX = RS * DS * SWP * (int)sizeof(SType);
-    static constexpr int B_LUT = 264 * 2;
+    static constexpr int B_LUT = 256 * 8 * 2;
     static constexpr int BYTES = B_BAR + B_RING + B_SX + B_LUT;
-    static_assert(32 % DS == 0 && XS % LPX == 0, "a consumer warp holds whole columns");
+    static_assert(DS % DPT == 0 && 32 % G == 0, "the threads of a column sit in adjacent lanes of one warp");
+    static_assert(DPT == 1 || DPT == 2 || DPT == 4, "ring entries are 4, 8 or 16 bytes");
     static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
-    static_assert(NC % 32 == 0 && NT <= 1024, "");
+    static_assert(NCT % 32 == 0 && NT <= 1024, "");
     static_assert(RS >= NPW, "every producer warp needs a slot of its own");
     static_assert(BYTES <= 232448, "tile exceeds shared memory");
 };
+
+template <int N> struct VecOf;
+template <> struct VecOf<1> { using type = uint32_t; };
+template <> struct VecOf<2> { using type = uint2; };
+template <> struct VecOf<4> { using type = uint4; };
+
+template <int N>
+__device__ __forceinline__ uint32_t &vget(typename VecOf<N>::type &v, int k);
+template <>
+__device__ __forceinline__ uint32_t &vget<1>(uint32_t &v, int) { return v; }
+template <>
+__device__ __forceinline__ uint32_t &vget<2>(uint2 &v, int k) { return k ? v.y : v.x; }
+template <>
+__device__ __forceinline__ uint32_t &vget<4>(uint4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
 
 template <class T>
 __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs a)
 {
     using SType = typename T::SType;
+    using Vec = typename VecOf<T::DPT>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + T::RS;
-    uint32_t *ring = reinterpret_cast<uint32_t *>(smem + T::B_BAR);
-    SType *sx = reinterpret_cast<SType *>(ring + kRing * T::NC);               // [RS][DS][SWP]
-    uint16_t *lut_ad = reinterpret_cast<uint16_t *>(sx + T::RS * T::DS * T::SWP);   // [256]
-    uint16_t *lut_mc = lut_ad + 256;                                              // [8]
+    Vec *ring = reinterpret_cast<Vec *>(smem + T::B_BAR);                     // [64][NCT]
+    SType *sx = reinterpret_cast<SType *>(smem + T::B_BAR + T::B_RING);       // [RS][DS][SWP]
+    uint16_t *lut = reinterpret_cast<uint16_t *>(smem + T::B_BAR + T::B_RING + T::B_SX);  // [256][8]
 
     const int t = threadIdx.x, lane = t & 31;
     const int X = a.X, Y = a.Y, D = a.D, wx = a.wx, wy = a.wy;
@@ -130,21 +154,35 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs
     const int d0 = blockIdx.y * T::DS;
     const uint32_t limit = a.wait_limit;
 
-    for (int i = t; i < 256; i += T::NT) lut_ad[i] = (uint16_t)a.lut_ad[i];
-    if (t < 8) lut_mc[t] = (uint16_t)a.lut_mc[t];   // index 7 never occurs
+    // combined cost table: AD(|grey difference|) + MC(Hamming), index ad * 8 + hamming
+    for (int i = t; i < 256 * 8; i += T::NT) lut[i] = (uint16_t)(a.lut_ad[i >> 3] + a.lut_mc[i & 7]);
     if (t == 0) {
         for (int s = 0; s < T::RS; ++s) {
             mbar_init(&full[s], 32);                // the producing warp
-            mbar_init(&empty[s], T::NC);            // every consumer
+            mbar_init(&empty[s], T::NCT);           // every consumer
         }
     }
     __syncthreads();
 
-    if (t >= T::NC) {
+    if (t >= T::NCT) {
         // ======================= producers: warp pw fills rows pw, pw+4, ...
-        const int pw = (t - T::NC) >> 5;
+        const int pw = (t - T::NCT) >> 5;
         const uint32_t P = a.P;
         const int xb = x0 - wx + lane * T::KE;      // x of this lane's first entry
+        // per-lane constants: clamped load offsets and, per (entry, disparity),
+        // whether the pixel and its match lie in the image
+        int offl[T::KE], offr[T::KE + T::DS - 1];
+        uint32_t inimg = 0;
+#pragma unroll
+        for (int k = 0; k < T::KE; ++k) offl[k] = min(max(xb + k, 0), X - 1);
+#pragma unroll
+        for (int k = 0; k < T::KE + T::DS - 1; ++k) offr[k] = min(max(xb + k - d0 - (T::DS - 1), 0), X - 1);
+#pragma unroll
+        for (int k = 0; k < T::KE; ++k)
+#pragma unroll
+            for (int q = 0; q < T::DS; ++q)
+                if (xb + k >= d0 + q && xb + k < X) inimg |= 1u << (k * T::DS + q);
+        const bool all_in = __all_sync(0xffffffffu, inimg == (1u << (T::KE * T::DS)) - 1u);
         for (int y = pw; y < Y; y += T::NPW) {
             const int s = y % T::RS;
             // loads first: they overlap the wait for the slot
@@ -152,10 +190,9 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs
             const uint32_t *pr = a.pix_r + (size_t)y * X;
             uint32_t pv[T::KE], qv[T::KE + T::DS - 1];
 #pragma unroll
-            for (int k = 0; k < T::KE; ++k) pv[k] = __ldg(pl + min(max(xb + k, 0), X - 1));
+            for (int k = 0; k < T::KE; ++k) pv[k] = __ldg(pl + offl[k]);
 #pragma unroll
-            for (int k = 0; k < T::KE + T::DS - 1; ++k)
-                qv[k] = __ldg(pr + min(max(xb + k - d0 - (T::DS - 1), 0), X - 1));
+            for (int k = 0; k < T::KE + T::DS - 1; ++k) qv[k] = __ldg(pr + offr[k]);
             if (y >= T::RS && !mbar_wait_warp(&empty[s], ((y / T::RS) - 1) & 1, limit, a.err)) return;
             uint32_t c[T::DS][T::KE];
             uint32_t run[T::DS];
@@ -163,15 +200,15 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs
             for (int q = 0; q < T::DS; ++q) run[q] = 0;
 #pragma unroll
             for (int k = 0; k < T::KE; ++k) {
-                const int xL = xb + k;
-                const uint32_t pw_ = pv[k];
+                const uint32_t pk = pv[k];
 #pragma unroll
                 for (int q = 0; q < T::DS; ++q) {
-                    // match of xL at disparity d0 + q is x = xL - d0 - q: qv index k + DS-1 - q
-                    const uint32_t qw = qv[k + T::DS - 1 - q];
-                    const int ad = abs((int)(pw_ & 0xFF) - (int)(qw & 0xFF));
-                    const uint32_t v = (uint32_t)lut_ad[ad] + lut_mc[__popc((pw_ ^ qw) >> 8)];
-                    run[q] += (xL >= d0 + q && xL < X) ? v : P;
+                    // match of entry k at disparity d0 + q: qv index k + DS-1 - q
+                    const uint32_t qk = qv[k + T::DS - 1 - q];
+                    const uint32_t ad = (uint32_t)abs((int)(pk & 0xFF) - (int)(qk & 0xFF));
+                    uint32_t v = lut[ad * 8 + __popc((pk ^ qk) & 0x3F00u)];
+                    if (!all_in) v = (inimg >> (k * T::DS + q)) & 1u ? v : P;
+                    run[q] += v;
                     c[q][k] = run[q];
                 }
             }
@@ -194,79 +231,92 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs
         return;
     }
 
-    // =========================== consumers
-    const int wc = t >> 5;
-    const int j = lane & (T::DS - 1);             // disparity index in the slab
-    const int xi = lane / T::DS;
-    constexpr int XG = T::XS / T::LPX;            // consumer warps per base
-    const int b = wc >= XG;
-    const int x = (wc - b * XG) * T::LPX + xi;
+    // =========================== consumers: thread (base, column, DPT disparities)
+    // thread t: group g = t mod G, column index t / G over both bases (a warp
+    // may hold columns of both bases; the G threads of a column never straddle
+    // warps since G divides 32)
+    const int g = t & (T::G - 1);                 // disparity group of this thread
+    const int ci = t / T::G;
+    const int b = ci >= T::XS;
+    const int x = ci - b * T::XS;
     const int col = b ? x0 - d0 + x : x0 + x;
     const bool valid = col >= 0 && col < X;
     const int colc = min(max(col, 0), X - 1);
-    const int d = d0 + j;
-    const uint32_t dkey = d < D ? (uint32_t)d : 0xFFFFFFFFu;
-    uint32_t *key = b ? a.key_r : a.key_l;
-    const uint32_t *arm = (b ? a.arm_r : a.arm_l) + colc;
-    uint32_t *myring = ring + t;
-    const int sbase = x + wx + (b ? j : 0);       // S index of this pixel's own column
+    const int dg = d0 + g * T::DPT;               // first disparity of the group
+    uint32_t *key = (b ? a.key_r : a.key_l) + colc;
+    // combined arm words: row r holds the left/right arms of row r (low half)
+    // and the up/down arms of row r - wy (high half)
+    const uint32_t *armc = (b ? a.armc_r : a.armc_l) + colc;
+    Vec *myring = ring + t;
+    // S element of this pixel's own column for the group's first disparity
+    const SType *srow0 = sx + (g * T::DPT) * T::SWP + x + wx + (b ? g * T::DPT : 0);
     const int rows = Y + wy;                      // row steps: inputs 0..Y-1, outputs lag by wy
 
-    // arm words of rows y (horizontal arms) and y - wy (vertical arms), three
-    // rows ahead in registers
-    uint32_t ah0, ah1, ah2, av0, av1, av2;
-    auto fetch = [&](int y, uint32_t &h, uint32_t &v) {
-        h = __ldg(arm + (size_t)min(y, Y - 1) * X);
-        v = __ldg(arm + (size_t)min(max(y - wy, 0), Y - 1) * X);
-    };
-    fetch(0, ah0, av0);
-    fetch(1, ah1, av1);
-
-    myring[0] = 0;                                // V(0) = 0
-    uint32_t V = 0;
-    auto step = [&](int y, uint32_t h, uint32_t v) -> bool {
+    uint32_t am0 = __ldg(armc), am1 = __ldg(armc + (size_t)min(1, rows - 1) * X), am2;
+    {
+        Vec z;
+#pragma unroll
+        for (int k = 0; k < T::DPT; ++k) vget<T::DPT>(z, k) = 0;
+        myring[0] = z;                            // V(0) = 0
+    }
+    uint32_t V[T::DPT];
+#pragma unroll
+    for (int k = 0; k < T::DPT; ++k) V[k] = 0;
+    auto step = [&](int y, uint32_t am) -> bool {
         const int s = y % T::RS;
-        const int yo = y - wy;
         if (y < Y) {
             if (!mbar_wait_warp(&full[s], (y / T::RS) & 1, limit, a.err)) return false;
-            const SType *row = sx + (s * T::DS + j) * T::SWP + sbase;
-            uint32_t cax = (uint32_t)row[((h >> 8) & 0xFF) + 1] - (uint32_t)row[-(int)(h & 0xFF)];
-            if (T::S16) cax &= 0xFFFFu;
-            V += cax;
-            myring[((y + 1) & (kRing - 1)) * T::NC] = V;
+            const SType *r0 = srow0 + s * (T::DS * T::SWP);
+            const int hi = ((am >> 8) & 0xFF) + 1, lo = am & 0xFF;
+            Vec w;
+#pragma unroll
+            for (int k = 0; k < T::DPT; ++k) {
+                const SType *rk = r0 + k * (T::SWP + (b ? 1 : 0));
+                uint32_t cax = (uint32_t)rk[hi] - (uint32_t)rk[-lo];
+                if (T::S16) cax &= 0xFFFFu;
+                V[k] += cax;
+                vget<T::DPT>(w, k) = V[k];
+            }
+            myring[((y + 1) & (kRing - 1)) * T::NCT] = w;
             mbar_arrive(&empty[s]);
         }
+        const int yo = y - wy;
         if (yo >= 0) {
-            const int up = (v >> 16) & 0xFF, down = v >> 24;
-            const uint32_t hi = myring[((yo + down + 1) & (kRing - 1)) * T::NC];
-            const uint32_t lo = myring[((yo - up) & (kRing - 1)) * T::NC];
-            uint32_t best = dkey == 0xFFFFFFFFu ? dkey : (((hi - lo) << 8) | dkey);
+            const int up = (am >> 16) & 0xFF, down = am >> 24;
+            Vec vh = myring[((yo + down + 1) & (kRing - 1)) * T::NCT];
+            Vec vl = myring[((yo - up) & (kRing - 1)) * T::NCT];
+            uint32_t best = 0xFFFFFFFFu;
 #pragma unroll
-            for (int o = 1; o < T::DS; o <<= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-            if (j == 0 && valid) atomicMin(key + (size_t)yo * X + col, best);
+            for (int k = 0; k < T::DPT; ++k) {
+                const uint32_t kk = ((vget<T::DPT>(vh, k) - vget<T::DPT>(vl, k)) << 8) | (uint32_t)(dg + k);
+                best = (dg + k < D) ? min(best, kk) : best;
+            }
+#pragma unroll
+            for (int o = 1; o < T::G; o <<= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (g == 0 && valid) atomicMin(key + (size_t)yo * X, best);
         }
         return true;
     };
     for (int y = 0; y < rows; y += 3) {
-        fetch(y + 2, ah2, av2);
-        if (!step(y, ah0, av0)) return;
+        am2 = __ldg(armc + (size_t)min(y + 2, rows - 1) * X);
+        if (!step(y, am0)) return;
         if (y + 1 >= rows) break;
-        fetch(y + 3, ah0, av0);
-        if (!step(y + 1, ah1, av1)) return;
+        am0 = __ldg(armc + (size_t)min(y + 3, rows - 1) * X);
+        if (!step(y + 1, am1)) return;
         if (y + 2 >= rows) break;
-        fetch(y + 4, ah1, av1);
-        if (!step(y + 2, ah2, av2)) return;
+        am1 = __ldg(armc + (size_t)min(y + 4, rows - 1) * X);
+        if (!step(y + 2, am2)) return;
     }
 }
 
 // Tile shapes (XS x DS). One CTA per SM; the ring of 64 prefix rows per
 // (column, disparity, base) dominates shared memory.
-using T0 = Tile<104, 4, 5, 8, true>;    // wx <= 26, window sums < 2^16
-using T1 = Tile<104, 4, 7, 6, true>;    // wx <= 29, window sums < 2^16
-using T2 = Tile<104, 4, 5, 4, false>;   // wx <= 26, 32-bit prefixes
-using T3 = Tile<104, 4, 7, 4, false>;   // wx <= 29, 32-bit prefixes
-using T4 = Tile<64, 4, 5, 8, true>;     // narrow frames
-using T5 = Tile<64, 4, 7, 4, false>;
+using T0 = Tile<104, 4, 5, 8, true, 2, 4>;    // wx <= 26, window sums < 2^16
+using T1 = Tile<104, 4, 7, 6, true, 2, 4>;    // wx <= 29, window sums < 2^16
+using T2 = Tile<104, 4, 5, 4, false, 2, 4>;   // wx <= 26, 32-bit prefixes
+using T3 = Tile<96, 4, 7, 4, false, 2, 4>;    // wx <= 29, 32-bit prefixes
+using T4 = Tile<96, 4, 5, 8, true, 4, 4>;     // one consumer thread per column
+using T5 = Tile<64, 4, 5, 8, true, 2, 4>;     // narrow frames
 
 template <class T>
 bool fits(const CostAggArgs &a)

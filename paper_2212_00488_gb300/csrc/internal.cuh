@@ -23,6 +23,8 @@ constexpr int kMaxWx = 29;
 struct CostAggArgs {
     const uint32_t *pix_l, *pix_r;   // [Y][X]
     const uint32_t *arm_l, *arm_r;   // [Y][X]
+    const uint32_t *armc_l, *armc_r; // [Y + wy][X]: low half arms of row r (left, right),
+                                     // high half arms of row r - wy (up, down)
     uint32_t *key_l, *key_r;         // [Y][X] min over d of (CA << 8 | d); preset to ~0
     const uint32_t *lut_ad;          // [256] quantised AD cost (Eq. 4) by |grey difference|
     const uint32_t *lut_mc;          // [8] quantised census cost (Eq. 5) by Hamming distance
@@ -47,8 +49,9 @@ cudaError_t launch_downscale(const uint8_t *g_l, const uint8_t *g_r, uint8_t *s_
 // Also presets the WTA keys of both bases to ~0 and clears the fused
 // kernel's error word for this frame.
 cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix_l, uint32_t *pix_r,
-                           uint32_t *arm_l, uint32_t *arm_r, uint32_t *key_l, uint32_t *key_r,
-                           uint32_t *err, int X, int Y, int wx, int wy, int tc, cudaStream_t s);
+                           uint32_t *arm_l, uint32_t *arm_r, uint32_t *armc_l, uint32_t *armc_r,
+                           uint32_t *key_l, uint32_t *key_r, uint32_t *err, int X, int Y, int wx, int wy,
+                           int tc, cudaStream_t s);
 cudaError_t launch_costagg(const CostAggArgs &a, cudaStream_t s);
 cudaError_t launch_refine(const uint32_t *key_l, const uint32_t *key_r, const uint8_t *grey_l,
                           int X, int Y, int T, uint8_t *dl, uint8_t *dr, uint8_t *gcp, uint8_t *dm,

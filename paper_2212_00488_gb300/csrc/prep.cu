@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kSupNT) support_kernel(
     const uint8_t *__restrict__ g_l, const uint8_t *__restrict__ g_r,
     uint32_t *__restrict__ pix_l, uint32_t *__restrict__ pix_r,
     uint32_t *__restrict__ arm_l, uint32_t *__restrict__ arm_r,
+    uint32_t *__restrict__ armc_l, uint32_t *__restrict__ armc_r,
     uint32_t *__restrict__ key_l, uint32_t *__restrict__ key_r, uint32_t *__restrict__ err,
     int X, int Y, int wx, int wy, int tc)
 {
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kSupNT) support_kernel(
     uint32_t *pix = blockIdx.z ? pix_r : pix_l;
     uint32_t *arm = blockIdx.z ? arm_r : arm_l;
     uint32_t *key = blockIdx.z ? key_r : key_l;
+    uint16_t *armc = reinterpret_cast<uint16_t *>(blockIdx.z ? armc_r : armc_l);
     const int hx = max(wx, 2), hy = max(wy, 1);
     const int TW = kSupTX + 2 * hx, TH = kSupTY + 2 * hy;
     const int x0 = blockIdx.x * kSupTX, y0 = blockIdx.y * kSupTY;
@@ -118,6 +120,10 @@ __global__ void __launch_bounds__(kSupNT) support_kernel(
         size_t idx = (size_t)y * X + x;
         pix[idx] = (uint32_t)c | (code << 8);
         arm[idx] = pack_arm(hm, hp, vm, vp);
+        // the fused kernel reads the left/right arms of row y together with
+        // the up/down arms of row y - wy, its output row
+        armc[2 * idx] = (uint16_t)(hm | (hp << 8));
+        armc[2 * ((size_t)(y + wy) * X + x) + 1] = (uint16_t)(vm | (vp << 8));
         key[idx] = 0xFFFFFFFFu;   // WTA key preset: the fused kernel takes atomic minima
     }
 }
@@ -159,14 +165,15 @@ cudaError_t launch_downscale(const uint8_t *g_l, const uint8_t *g_r, uint8_t *s_
 }
 
 cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix_l, uint32_t *pix_r,
-                           uint32_t *arm_l, uint32_t *arm_r, uint32_t *key_l, uint32_t *key_r,
-                           uint32_t *err, int X, int Y, int wx, int wy, int tc, cudaStream_t s)
+                           uint32_t *arm_l, uint32_t *arm_r, uint32_t *armc_l, uint32_t *armc_r,
+                           uint32_t *key_l, uint32_t *key_r, uint32_t *err, int X, int Y, int wx, int wy,
+                           int tc, cudaStream_t s)
 {
     const int hx = wx > 2 ? wx : 2, hy = wy > 1 ? wy : 1;
     size_t smem = (size_t)(kSupTX + 2 * hx) * (kSupTY + 2 * hy);
     dim3 grid((X + kSupTX - 1) / kSupTX, (Y + kSupTY - 1) / kSupTY, 2);
-    support_kernel<<<grid, kSupNT, smem, s>>>(g_l, g_r, pix_l, pix_r, arm_l, arm_r, key_l, key_r, err, X, Y,
-                                               wx, wy, tc);
+    support_kernel<<<grid, kSupNT, smem, s>>>(g_l, g_r, pix_l, pix_r, arm_l, arm_r, armc_l, armc_r, key_l,
+                                               key_r, err, X, Y, wx, wy, tc);
     return cudaGetLastError();
 }
 

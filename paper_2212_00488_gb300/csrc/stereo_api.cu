@@ -24,7 +24,7 @@ struct stereo_ctx {
     uint32_t *d_lut = nullptr;
     uint32_t *d_err = nullptr;      // device error word of the fused kernel's bounded waits
     uint32_t *h_err = nullptr;      // pinned host copy
-    uint32_t wait_limit = 1u << 22;
+    uint32_t wait_limit = 1u << 20;
 
     void *ws = nullptr;
     size_t ws_size = 0;
@@ -36,6 +36,7 @@ struct stereo_ctx {
     uint8_t *gs[2] = {nullptr, nullptr};   // processed grey
     uint32_t *pix[2] = {nullptr, nullptr};
     uint32_t *arm[2] = {nullptr, nullptr};
+    uint32_t *armc[2] = {nullptr, nullptr};   // [Y + wy][X] arm words of the fused kernel
     uint32_t *key[2] = {nullptr, nullptr};
     uint8_t *dm = nullptr;
     float *dplus_ws = nullptr;
@@ -158,6 +159,7 @@ size_t layout(stereo_ctx *c, char *base, int W, int H, bool staging)
     for (int i = 0; i < 2; ++i) c->gs[i] = ds ? (uint8_t *)take(nl) : c->gf[i];
     for (int i = 0; i < 2; ++i) c->pix[i] = (uint32_t *)take(nl * 4);
     for (int i = 0; i < 2; ++i) c->arm[i] = (uint32_t *)take(nl * 4);
+    for (int i = 0; i < 2; ++i) c->armc[i] = (uint32_t *)take((size_t)X * (Y + c->p.wy) * 4);
     for (int i = 0; i < 2; ++i) c->key[i] = (uint32_t *)take(nl * 4);
     c->dm = (uint8_t *)take(nl);
     c->dplus_ws = (float *)take(nl * 4);
@@ -231,14 +233,17 @@ cudaError_t run_stage(stereo_ctx *c, int stage, cudaStream_t s)
     }
     case STEREO_STAGE_SUPPORT:
         c->launches++;
-        return launch_support(c->gs[0], c->gs[1], c->pix[0], c->pix[1], c->arm[0], c->arm[1], c->key[0],
-                              c->key[1], c->d_err, c->X, c->Y, c->p.wx, c->p.wy, c->p.tc, s);
+        return launch_support(c->gs[0], c->gs[1], c->pix[0], c->pix[1], c->arm[0], c->arm[1], c->armc[0],
+                              c->armc[1], c->key[0], c->key[1], c->d_err, c->X, c->Y, c->p.wx, c->p.wy,
+                              c->p.tc, s);
     case STEREO_STAGE_COSTAGG: {
         CostAggArgs a;
         a.pix_l = c->pix[0];
         a.pix_r = c->pix[1];
         a.arm_l = c->arm[0];
         a.arm_r = c->arm[1];
+        a.armc_l = c->armc[0];
+        a.armc_r = c->armc[1];
         a.key_l = c->key[0];
         a.key_r = c->key[1];
         a.lut_ad = c->d_lut;

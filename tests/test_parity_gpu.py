@@ -222,7 +222,7 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
     with pytest.raises(_lib.StereoError) as e:
         _lib.stereo_sync(st.ctx)
     assert e.value.code == _lib.STEREO_ETIMEOUT
-    _lib.stereo_set_wait_limit(st.ctx, 1 << 22)
+    _lib.stereo_set_wait_limit(st.ctx, 1 << 20)
     out = st(lt, rt, 30, maps=True)
     torch.cuda.synchronize()
     _lib.stereo_sync(st.ctx)
