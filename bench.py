@@ -40,6 +40,24 @@ SM_COUNT_NOMINAL = 152
 LANES_PER_SM = 128              # 4 SM sub-partitions x 32 lanes issue one warp instruction per clock each
 
 
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "costagg_wta_kernel_1436x992_d145_traffic.txt")
+COSTAGG_SRC = os.path.join(ROOT, "paper_2212_00488_gb300", "csrc", "costagg.cu")
+
+
+def _recorded_traffic():
+    """DRAM bytes per launch of the fused kernel from its last ncu capture, or
+    None when the kernel source has changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            rec = json.load(f)
+        with open(COSTAGG_SRC, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    return rec["traffic_bytes_per_launch"] if rec.get("source_sha256") == h else None
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -272,7 +290,8 @@ def run_ours(args):
             "stage_ms": dict(zip(_lib.STAGE_NAMES, [round(t, 5) for t in stage_ms])),
             "roofline": {"bound": "alu", "kernel": "costagg_wta_kernel", "achieved": achieved / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": achieved / peak_ops,
-                         "traffic": None,
+                         "traffic": _recorded_traffic(),
+                         "traffic_unit": "bytes per launch (dram read + write, ncu)",
                          "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz (issue limit, "
                                         f"max clock from {src} peaks)",
                          "ops_per_cell": OPS_PER_CELL, "cells_per_launch": cells,

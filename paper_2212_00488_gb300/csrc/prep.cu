@@ -62,38 +62,43 @@ __global__ void downscale_kernel(const uint8_t *__restrict__ g_l, const uint8_t 
     s[(size_t)y * X + x] = (uint8_t)((sum + 4) / 9);
 }
 
-constexpr int kSupTX = 64;   // output tile of the support kernel
-constexpr int kSupTY = 8;
+// Support data in two passes, each with a halo only along its own axis.
+//  Pass H: rows of kHX pixels (plus wx or 2 pixels each side and one row
+//  above and below): census code and left/right arms; grey | census << 8 goes
+//  to the pixel word, the left/right arms to the low half of the arm words.
+//  Pass V: columns of kVY pixels (plus wy rows above and below): up/down arms
+//  to the high half of the arm words.
+// Coordinates of the staged tiles are clamped to the image (border
+// replication, which census reads); the arm scans stop at the real border.
+constexpr int kHX = 256;   // pass H: outputs per row tile
+constexpr int kHY = 4;     // pass H: rows per CTA
+constexpr int kVX = 32;    // pass V: columns per CTA
+constexpr int kVY = 32;    // pass V: outputs per column tile
 constexpr int kSupNT = 256;
 
-// Mini-census code and cross arms of every pixel of one image (blockIdx.z).
-// The tile plus a halo of max(wx, 2) columns and max(wy, 1) rows is staged in
-// shared memory with clamped coordinates; census reads the clamped copies
-// (border replication), while the arm scans stop at the real image border.
-__global__ void __launch_bounds__(kSupNT) support_kernel(
+__global__ void __launch_bounds__(kSupNT) support_h_kernel(
     const uint8_t *__restrict__ g_l, const uint8_t *__restrict__ g_r,
     uint32_t *__restrict__ pix_l, uint32_t *__restrict__ pix_r,
     uint32_t *__restrict__ arm_l, uint32_t *__restrict__ arm_r,
     uint32_t *__restrict__ armc_l, uint32_t *__restrict__ armc_r,
     uint32_t *__restrict__ key_l, uint32_t *__restrict__ key_r, uint32_t *__restrict__ err,
-    int X, int Y, int wx, int wy, int tc)
+    int X, int Y, int wx, int tc)
 {
     extern __shared__ uint8_t tile[];
     const uint8_t *g = blockIdx.z ? g_r : g_l;
     uint32_t *pix = blockIdx.z ? pix_r : pix_l;
-    uint32_t *arm = blockIdx.z ? arm_r : arm_l;
-    uint32_t *key = blockIdx.z ? key_r : key_l;
+    uint16_t *arm = reinterpret_cast<uint16_t *>(blockIdx.z ? arm_r : arm_l);
     uint16_t *armc = reinterpret_cast<uint16_t *>(blockIdx.z ? armc_r : armc_l);
-    const int hx = max(wx, 2), hy = max(wy, 1);
-    const int TW = kSupTX + 2 * hx, TH = kSupTY + 2 * hy;
-    const int x0 = blockIdx.x * kSupTX, y0 = blockIdx.y * kSupTY;
+    uint32_t *key = blockIdx.z ? key_r : key_l;
+    const int hx = max(wx, 2);
+    const int TW = kHX + 2 * hx, TH = kHY + 2;
+    const int x0 = blockIdx.x * kHX, y0 = blockIdx.y * kHY;
     if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *err = 0u;
 
-    for (int i = threadIdx.x; i < TW * TH; i += kSupNT) {
-        int ty = i / TW, tx = i - ty * TW;
-        int gx = min(max(x0 - hx + tx, 0), X - 1);
-        int gy = min(max(y0 - hy + ty, 0), Y - 1);
-        tile[i] = __ldg(g + (size_t)gy * X + gx);
+    for (int ty = 0; ty < TH; ++ty) {
+        const uint8_t *row = g + (size_t)min(max(y0 - 1 + ty, 0), Y - 1) * X;
+        for (int tx = threadIdx.x; tx < TW; tx += kSupNT)
+            tile[ty * TW + tx] = __ldg(row + min(max(x0 - hx + tx, 0), X - 1));
     }
     __syncthreads();
 
@@ -101,30 +106,60 @@ __global__ void __launch_bounds__(kSupNT) support_kernel(
     // mirror-symmetric in x; bit k set when neighbour k is strictly darker.
     const int cdx[6] = {-1, +1, -2, +2, -1, +1};
     const int cdy[6] = {-1, -1, 0, 0, +1, +1};
-
-    for (int o = threadIdx.x; o < kSupTX * kSupTY; o += kSupNT) {
-        int oy = o / kSupTX, ox = o - oy * kSupTX;
-        int x = x0 + ox, y = y0 + oy;
-        if (x >= X || y >= Y) continue;
-        const int tx = ox + hx, ty = oy + hy;
-        const uint8_t *t = tile + ty * TW + tx;
-        int c = t[0];
-        uint32_t code = 0;
+    for (int oy = 0; oy < kHY; ++oy) {
+        const int y = y0 + oy;
+        if (y >= Y) break;
+        for (int ox = threadIdx.x; ox < kHX; ox += kSupNT) {
+            const int x = x0 + ox;
+            if (x >= X) break;
+            const uint8_t *t = tile + (oy + 1) * TW + ox + hx;
+            const int c = t[0];
+            uint32_t code = 0;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) code |= (uint32_t)(t[cdy[k] * TW + cdx[k]] < c) << k;
-        int hm = 0, hp = 0, vm = 0, vp = 0;
-        while (hm < wx && x - hm - 1 >= 0 && abs((int)t[-(hm + 1)] - c) < tc) ++hm;
-        while (hp < wx && x + hp + 1 < X && abs((int)t[hp + 1] - c) < tc) ++hp;
-        while (vm < wy && y - vm - 1 >= 0 && abs((int)t[-(vm + 1) * TW] - c) < tc) ++vm;
-        while (vp < wy && y + vp + 1 < Y && abs((int)t[(vp + 1) * TW] - c) < tc) ++vp;
-        size_t idx = (size_t)y * X + x;
-        pix[idx] = (uint32_t)c | (code << 8);
-        arm[idx] = pack_arm(hm, hp, vm, vp);
-        // the fused kernel reads the left/right arms of row y together with
-        // the up/down arms of row y - wy, its output row
-        armc[2 * idx] = (uint16_t)(hm | (hp << 8));
-        armc[2 * ((size_t)(y + wy) * X + x) + 1] = (uint16_t)(vm | (vp << 8));
-        key[idx] = 0xFFFFFFFFu;   // WTA key preset: the fused kernel takes atomic minima
+            for (int k = 0; k < 6; ++k) code |= (uint32_t)(t[cdy[k] * TW + cdx[k]] < c) << k;
+            int hm = 0, hp = 0;
+            while (hm < wx && x - hm - 1 >= 0 && abs((int)t[-(hm + 1)] - c) < tc) ++hm;
+            while (hp < wx && x + hp + 1 < X && abs((int)t[hp + 1] - c) < tc) ++hp;
+            const size_t idx = (size_t)y * X + x;
+            pix[idx] = (uint32_t)c | (code << 8);
+            const uint16_t h = (uint16_t)(hm | (hp << 8));
+            arm[2 * idx] = h;
+            armc[2 * idx] = h;      // the fused kernel reads row y's left/right arms in row y
+            key[idx] = 0xFFFFFFFFu; // WTA key preset: the fused kernel takes atomic minima
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSupNT) support_v_kernel(
+    const uint8_t *__restrict__ g_l, const uint8_t *__restrict__ g_r,
+    uint32_t *__restrict__ arm_l, uint32_t *__restrict__ arm_r,
+    uint32_t *__restrict__ armc_l, uint32_t *__restrict__ armc_r, int X, int Y, int wy, int tc)
+{
+    extern __shared__ uint8_t tile[];
+    const uint8_t *g = blockIdx.z ? g_r : g_l;
+    uint16_t *arm = reinterpret_cast<uint16_t *>(blockIdx.z ? arm_r : arm_l);
+    uint16_t *armc = reinterpret_cast<uint16_t *>(blockIdx.z ? armc_r : armc_l);
+    const int hy = max(wy, 1);
+    const int TH = kVY + 2 * hy;
+    const int x0 = blockIdx.x * kVX, y0 = blockIdx.y * kVY;
+    const int tx = threadIdx.x % kVX, tq = threadIdx.x / kVX;     // kSupNT / kVX threads per column
+    const int x = min(x0 + tx, X - 1);
+    for (int ty = tq; ty < TH; ty += kSupNT / kVX)
+        tile[ty * kVX + tx] = __ldg(g + (size_t)min(max(y0 - hy + ty, 0), Y - 1) * X + x);
+    __syncthreads();
+    if (x0 + tx >= X) return;
+    for (int oy = tq; oy < kVY; oy += kSupNT / kVX) {
+        const int y = y0 + oy;
+        if (y >= Y) break;
+        const uint8_t *t = tile + (oy + hy) * kVX + tx;
+        const int c = t[0];
+        int vm = 0, vp = 0;
+        while (vm < wy && y - vm - 1 >= 0 && abs((int)t[-(vm + 1) * kVX] - c) < tc) ++vm;
+        while (vp < wy && y + vp + 1 < Y && abs((int)t[(vp + 1) * kVX] - c) < tc) ++vp;
+        const uint16_t v = (uint16_t)(vm | (vp << 8));
+        arm[2 * ((size_t)y * X + x) + 1] = v;
+        // the fused kernel reads the up/down arms of output row y in row y + wy
+        armc[2 * ((size_t)(y + wy) * X + x) + 1] = v;
     }
 }
 
@@ -170,10 +205,14 @@ cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix
                            int tc, cudaStream_t s)
 {
     const int hx = wx > 2 ? wx : 2, hy = wy > 1 ? wy : 1;
-    size_t smem = (size_t)(kSupTX + 2 * hx) * (kSupTY + 2 * hy);
-    dim3 grid((X + kSupTX - 1) / kSupTX, (Y + kSupTY - 1) / kSupTY, 2);
-    support_kernel<<<grid, kSupNT, smem, s>>>(g_l, g_r, pix_l, pix_r, arm_l, arm_r, armc_l, armc_r, key_l,
-                                               key_r, err, X, Y, wx, wy, tc);
+    dim3 gh((X + kHX - 1) / kHX, (Y + kHY - 1) / kHY, 2);
+    support_h_kernel<<<gh, kSupNT, (size_t)(kHX + 2 * hx) * (kHY + 2), s>>>(
+        g_l, g_r, pix_l, pix_r, arm_l, arm_r, armc_l, armc_r, key_l, key_r, err, X, Y, wx, tc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 gv((X + kVX - 1) / kVX, (Y + kVY - 1) / kVY, 2);
+    support_v_kernel<<<gv, kSupNT, (size_t)kVX * (kVY + 2 * hy), s>>>(g_l, g_r, arm_l, arm_r, armc_l, armc_r,
+                                                                       X, Y, wy, tc);
     return cudaGetLastError();
 }
 

@@ -232,7 +232,7 @@ cudaError_t run_stage(stereo_ctx *c, int stage, cudaStream_t s)
         return launch_downscale(c->gf[0], c->gf[1], c->gs[0], c->gs[1], c->W, c->H, s);
     }
     case STEREO_STAGE_SUPPORT:
-        c->launches++;
+        c->launches += 2;
         return launch_support(c->gs[0], c->gs[1], c->pix[0], c->pix[1], c->arm[0], c->arm[1], c->armc[0],
                               c->armc[1], c->key[0], c->key[1], c->d_err, c->X, c->Y, c->p.wx, c->p.wy,
                               c->p.tc, s);
