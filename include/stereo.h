@@ -183,6 +183,38 @@ STEREO_API int stereo_set_tile(stereo_ctx *ctx, int tile);
 /* The tile shape a compute of this frame shape would use (>= 0), or EINVAL. */
 STEREO_API int stereo_get_tile(stereo_ctx *ctx, int W, int H, int Dmax);
 
+/* stereo_compute without any allocation at call time. The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory while they run, such as a real-time frame loop that may not
+ * stall on, or fail in, an allocation, or a program whose memory pool owns the
+ * device and forbids other allocations. It needs no context.
+ *
+ * All intermediates live in one fixed 32 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits. A
+ * frame fits when its workspace does: with the default parameters that is
+ * about 11.8 bytes per input pixel with downscaling (1436x992 needs 17 MB; up
+ * to about 2.8 Mpixel) and about 43 bytes per pixel without it (up to about
+ * 0.78 Mpixel). A larger frame is rejected with STEREO_ENOMEM and a message in
+ * err. Nothing is allocated: no cudaMalloc, cudaFree or allocating library
+ * call.
+ *
+ *  params: NULL for stereo_default_params().
+ *  left_rgb, right_rgb, W, H, Dmax, disp_out, dl_out, dr_out, gcp_out,
+ *    stream: as for stereo_compute, on the current CUDA device; stream NULL
+ *    is the legacy default stream.
+ *  err, err_len: optional buffer for a one-line message on failure.
+ * The first call on a device looks up the array's device address and sets the
+ * kernels' attributes; make that first call before any stream capture. The
+ * cost tables are copied from host memory, so a call may wait for work
+ * already queued on its stream. Every call shares the one array and its
+ * contents stay from the last call: calls whose work overlaps on the GPU (on
+ * different streams or host threads) race and give wrong maps. A bounded wait
+ * that gives up inside the fused kernel is not reported by this entry point. */
+STEREO_API int stereo_compute_noalloc(const stereo_params *params, const uint8_t *left_rgb,
+                                      const uint8_t *right_rgb, int W, int H, int Dmax, float *disp_out,
+                                      uint8_t *dl_out, uint8_t *dr_out, uint8_t *gcp_out, void *stream,
+                                      char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,6 +61,8 @@ _SIGNATURES = {
     "stereo_set_tile": (_i, [_ctxp, _i]),
     "stereo_get_tile": (_i, [_ctxp, _i, _i, _i]),
     "stereo_set_wait_limit": (_i, [_ctxp, ctypes.c_uint32]),
+    "stereo_compute_noalloc": (_i, [ctypes.POINTER(stereo_params), _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp,
+                                    _vp, ctypes.c_char_p, ctypes.c_size_t]),
 }
 
 _lib = None
