@@ -233,11 +233,10 @@ def run_ours(args):
     stage_ms, nframes = _lib.stereo_stage_ms(st.ctx)
     _lib.stereo_set_profiling(st.ctx, False)
 
-    t_local = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    fps = world * args.steps / (ms_max / 1e3)
+    from paper_2212_00488_gb300 import replicas
+    agg = replicas.aggregate(float(args.steps), ms_total / 1e3)
+    ms_max = agg.seconds_max * 1e3
+    fps = agg.throughput
 
     # e2e through the host-buffer entry point, pinned host memory
     hl = [torch.from_numpy(p.left).pin_memory() for p in pool[:4]]
@@ -252,10 +251,7 @@ def run_ours(args):
     for i in range(e2e_steps):
         st.compute_host(hl[i % 4], hr[i % 4], DMAX, hdisp)
     e2e_dt = time.perf_counter() - t0
-    t_e2e = torch.tensor([e2e_dt], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_fps = world * e2e_steps / float(t_e2e.item())
+    e2e_fps = replicas.aggregate(float(e2e_steps), e2e_dt).throughput
 
     if rank == 0:
         peaks, src = _peaks()
