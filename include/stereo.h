@@ -183,6 +183,43 @@ STEREO_API int stereo_set_tile(stereo_ctx *ctx, int tile);
 /* The tile shape a compute of this frame shape would use (>= 0), or EINVAL. */
 STEREO_API int stereo_get_tile(stereo_ctx *ctx, int W, int H, int Dmax);
 
+/* One frame of a batch (stereo_compute_batch): the arguments of
+ * stereo_compute for one pair. Frames of a batch may differ in W, H and Dmax. */
+typedef struct {
+    const uint8_t *left_rgb;   /* device, H*W*3 bytes */
+    const uint8_t *right_rgb;  /* device, H*W*3 bytes */
+    int W, H, Dmax;
+    float *disp_out;           /* device, required */
+    uint8_t *dl_out, *dr_out, *gcp_out;   /* device, optional (NULL) */
+} stereo_job;
+
+/* Up to 32 pairs in one call (the batched form of the method; the paper
+ * processes one pair at a time). Preparation and post-processing run per
+ * frame, the fused cost + aggregation + WTA of all frames runs as one
+ * persistent kernel taking (frame, strip, slab) tiles largest frame first;
+ * the whole batch is one CUDA graph, re-captured and updated in place on each
+ * call. Each frame's maps equal stereo_compute's for that frame exactly.
+ * With the automatic tile (stereo_set_tile(-1)) the first batch of a given
+ * signature (frame shapes, parameters, GPU) times every tile shape that fits
+ * and remembers the fastest; stereo_tune_save / stereo_tune_load keep those
+ * choices across processes. Asynchronous on `stream` (NULL: the context's
+ * stream). The batch uses a workspace of its own next to the single-frame
+ * one; both count against the memory cap. */
+STEREO_API int stereo_compute_batch(stereo_ctx *ctx, int n, const stereo_job *jobs, void *stream);
+
+/* Tile shape used by the last batch (-1 if none); when tune_ms is not NULL
+ * it receives, for up to n tile ids, the autotuner's time of that shape in
+ * ms (-1 where it did not fit or no tuning ran in that call). */
+STEREO_API int stereo_batch_tile(const stereo_ctx *ctx, float *tune_ms, int n);
+
+/* Writes the autotuner's choices (one "signature<TAB>tile" line each) to a
+ * text file; returns the number written or EINVAL. */
+STEREO_API int stereo_tune_save(stereo_ctx *ctx, const char *path);
+
+/* Adds the choices of a file written by stereo_tune_save; returns how many
+ * were read or EINVAL. */
+STEREO_API int stereo_tune_load(stereo_ctx *ctx, const char *path);
+
 /* stereo_compute without any allocation at call time. The paper has no
  * counterpart: this entry point exists for callers that must not allocate
  * device memory while they run, such as a real-time frame loop that may not

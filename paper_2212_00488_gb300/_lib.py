@@ -28,6 +28,20 @@ NUM_STAGES = 5
 STAGE_NAMES = ["SD", "W+-/W*+-", "C+CA_x+CA", "CC+Post", "SU"]
 
 
+class stereo_job(ctypes.Structure):
+    _fields_ = [
+        ("left_rgb", ctypes.c_void_p),
+        ("right_rgb", ctypes.c_void_p),
+        ("W", ctypes.c_int),
+        ("H", ctypes.c_int),
+        ("Dmax", ctypes.c_int),
+        ("disp_out", ctypes.c_void_p),
+        ("dl_out", ctypes.c_void_p),
+        ("dr_out", ctypes.c_void_p),
+        ("gcp_out", ctypes.c_void_p),
+    ]
+
+
 class stereo_params(ctypes.Structure):
     _fields_ = [
         ("lambda_ad", ctypes.c_double),
@@ -61,6 +75,10 @@ _SIGNATURES = {
     "stereo_set_tile": (_i, [_ctxp, _i]),
     "stereo_get_tile": (_i, [_ctxp, _i, _i, _i]),
     "stereo_set_wait_limit": (_i, [_ctxp, ctypes.c_uint32]),
+    "stereo_compute_batch": (_i, [_ctxp, _i, ctypes.c_void_p, _vp]),
+    "stereo_batch_tile": (_i, [_ctxp, ctypes.POINTER(ctypes.c_float), _i]),
+    "stereo_tune_save": (_i, [_ctxp, ctypes.c_char_p]),
+    "stereo_tune_load": (_i, [_ctxp, ctypes.c_char_p]),
     "stereo_compute_noalloc": (_i, [ctypes.POINTER(stereo_params), _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp,
                                     _vp, ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -173,6 +191,33 @@ def stereo_set_wait_limit(ctx, polls):
 
 def stereo_get_tile(ctx, W, H, dmax):
     rc = load().stereo_get_tile(ctx, W, H, dmax)
+    if rc < 0:
+        check(ctx, rc)
+    return rc
+
+
+def stereo_compute_batch(ctx, jobs, stream=0):
+    """jobs: a sequence of stereo_job structures."""
+    arr = (stereo_job * len(jobs))(*jobs)
+    return check(ctx, load().stereo_compute_batch(ctx, len(jobs), ctypes.cast(arr, ctypes.c_void_p), stream or None))
+
+
+def stereo_batch_tile(ctx):
+    """(tile of the last batch, autotuner ms per tile id or -1)."""
+    buf = (ctypes.c_float * NUM_TILES)()
+    t = load().stereo_batch_tile(ctx, buf, NUM_TILES)
+    return t, list(buf)
+
+
+def stereo_tune_save(ctx, path):
+    rc = load().stereo_tune_save(ctx, path.encode())
+    if rc < 0:
+        check(ctx, rc)
+    return rc
+
+
+def stereo_tune_load(ctx, path):
+    rc = load().stereo_tune_load(ctx, path.encode())
     if rc < 0:
         check(ctx, rc)
     return rc

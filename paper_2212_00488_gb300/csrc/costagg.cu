@@ -115,7 +115,7 @@ struct Tile {
     static constexpr int B_LUT = 256 * 8 * 2;
     static constexpr int BYTES = B_BAR + B_RING + B_SX + B_LUT;
     static_assert(DS % DPT == 0 && 32 % G == 0, "the threads of a column sit in adjacent lanes of one warp");
-    static_assert(DPT == 1 || DPT == 2 || DPT == 4, "ring entries are 4, 8 or 16 bytes");
+    static_assert(DPT == 2 || DPT == 4, "ring entries are 8 or 16 bytes");
     static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
     static_assert(NCT % 32 == 0 && NT <= 1024, "");
     static_assert(RS >= NPW, "every producer warp needs a slot of its own");
@@ -123,25 +123,30 @@ struct Tile {
 };
 
 template <int N> struct VecOf;
-template <> struct VecOf<1> { using type = uint32_t; };
 template <> struct VecOf<2> { using type = uint2; };
 template <> struct VecOf<4> { using type = uint4; };
 
 template <int N>
 __device__ __forceinline__ uint32_t &vget(typename VecOf<N>::type &v, int k);
 template <>
-__device__ __forceinline__ uint32_t &vget<1>(uint32_t &v, int) { return v; }
-template <>
 __device__ __forceinline__ uint32_t &vget<2>(uint2 &v, int k) { return k ? v.y : v.x; }
 template <>
 __device__ __forceinline__ uint32_t &vget<4>(uint4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
 
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// One tile (x-strip from x0, disparity slab from d0) of one frame. `reuse`
+// is set when this CTA already ran a tile: its barriers are invalidated before
+// they are initialised again and the cost table is already in place.
 template <class T>
-__global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs a)
+__device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0, const int d0,
+                                             unsigned char *smem, const bool reuse)
 {
     using SType = typename T::SType;
     using Vec = typename VecOf<T::DPT>::type;
-    extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + T::RS;
     Vec *ring = reinterpret_cast<Vec *>(smem + T::B_BAR);                     // [64][NCT]
@@ -150,14 +155,17 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs
 
     const int t = threadIdx.x, lane = t & 31;
     const int X = a.X, Y = a.Y, D = a.D, wx = a.wx, wy = a.wy;
-    const int x0 = blockIdx.x * T::XS;
-    const int d0 = blockIdx.y * T::DS;
     const uint32_t limit = a.wait_limit;
 
     // combined cost table: AD(|grey difference|) + MC(Hamming), index ad * 8 + hamming
-    for (int i = t; i < 256 * 8; i += T::NT) lut[i] = (uint16_t)(a.lut_ad[i >> 3] + a.lut_mc[i & 7]);
+    if (!reuse)
+        for (int i = t; i < 256 * 8; i += T::NT) lut[i] = (uint16_t)(a.lut_ad[i >> 3] + a.lut_mc[i & 7]);
     if (t == 0) {
         for (int s = 0; s < T::RS; ++s) {
+            if (reuse) {
+                mbar_inval(&full[s]);
+                mbar_inval(&empty[s]);
+            }
             mbar_init(&full[s], 32);                // the producing warp
             mbar_init(&empty[s], T::NCT);           // every consumer
         }
@@ -309,6 +317,41 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs
     }
 }
 
+template <class T>
+__global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    costagg_tile<T>(a, blockIdx.x * T::XS, blockIdx.y * T::DS, smem, false);
+}
+
+// Persistent form for a batch of frames: one CTA per SM takes tiles (job,
+// strip, slab) from a global counter until none is left. Jobs come largest
+// first, so the long sweeps start early and the short ones fill the tail.
+template <class T>
+__global__ void __launch_bounds__(T::NT, 1) costagg_batch_kernel(const __grid_constant__ BatchArgs b)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tile;
+    bool reuse = false;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            // stop taking tiles once a bounded wait has given up anywhere
+            const bool failed = *(volatile uint32_t *)b.job[0].err != 0u;
+            s_tile = failed ? b.total_tiles : (int)atomicAdd(b.counter, 1u);
+        }
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= b.total_tiles) return;
+        int j = 0;
+        while (j + 1 < b.njobs && tile >= b.tile_start[j + 1]) ++j;
+        const int local = tile - b.tile_start[j];
+        const int strip = local % b.nstrip[j], slab = local / b.nstrip[j];
+        costagg_tile<T>(b.job[j], strip * T::XS, slab * T::DS, smem, reuse);
+        reuse = true;
+        __syncthreads();
+    }
+}
+
 // Tile shapes (XS x DS). One CTA per SM; the ring of 64 prefix rows per
 // (column, disparity, base) dominates shared memory.
 using T0 = Tile<104, 4, 5, 8, true, 2, 4>;    // wx <= 26, window sums < 2^16
@@ -327,18 +370,42 @@ bool fits(const CostAggArgs &a)
 }
 
 template <class T>
-cudaError_t setup_one()
-{
-    return cudaFuncSetAttribute(costagg_wta_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::BYTES);
-}
-
-template <class T>
 void grid_of(const CostAggArgs &a, int &nstrip, int &nslab)
 {
     nslab = (a.D + T::DS - 1) / T::DS;
     const int dlast = (nslab - 1) * T::DS;
     nstrip = (a.X + dlast + T::XS - 1) / T::XS;
 }
+
+template <class T>
+cudaError_t setup_one()
+{
+    cudaError_t e = cudaFuncSetAttribute(costagg_wta_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         T::BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(costagg_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::BYTES);
+}
+
+template <class T>
+cudaError_t launch_batch_one(BatchArgs &b, int nsm, cudaStream_t s)
+{
+    b.total_tiles = 0;
+    for (int j = 0; j < b.njobs; ++j) {
+        if (!fits<T>(b.job[j])) return cudaErrorInvalidValue;
+        int nstrip, nslab;
+        grid_of<T>(b.job[j], nstrip, nslab);
+        b.nstrip[j] = nstrip;
+        b.tile_start[j] = b.total_tiles;
+        b.total_tiles += nstrip * nslab;
+    }
+    b.tile_start[b.njobs] = b.total_tiles;
+    cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const int grid = b.total_tiles < nsm ? b.total_tiles : nsm;
+    costagg_batch_kernel<T><<<grid, T::NT, T::BYTES, s>>>(b);
+    return cudaGetLastError();
+}
+
 
 template <class T>
 cudaError_t launch_one(const CostAggArgs &a, cudaStream_t s)
@@ -388,6 +455,33 @@ int costagg_pick(const CostAggArgs &a, int nsm)
     consider(4, fits<T4>(a), estimate<T4>(a, nsm));
     consider(5, fits<T5>(a), estimate<T5>(a, nsm) * 1.01);
     return best;
+}
+
+bool costagg_fits(const CostAggArgs &a, int tile)
+{
+    switch (tile) {
+    case 0: return fits<T0>(a);
+    case 1: return fits<T1>(a);
+    case 2: return fits<T2>(a);
+    case 3: return fits<T3>(a);
+    case 4: return fits<T4>(a);
+    case 5: return fits<T5>(a);
+    default: return false;
+    }
+}
+
+cudaError_t launch_costagg_batch(BatchArgs &b, int tile, int nsm, cudaStream_t s)
+{
+    if (b.njobs < 1 || b.njobs > kMaxBatch) return cudaErrorInvalidValue;
+    switch (tile) {
+    case 0: return launch_batch_one<T0>(b, nsm, s);
+    case 1: return launch_batch_one<T1>(b, nsm, s);
+    case 2: return launch_batch_one<T2>(b, nsm, s);
+    case 3: return launch_batch_one<T3>(b, nsm, s);
+    case 4: return launch_batch_one<T4>(b, nsm, s);
+    case 5: return launch_batch_one<T5>(b, nsm, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_costagg(const CostAggArgs &a, cudaStream_t s)

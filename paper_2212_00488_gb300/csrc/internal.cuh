@@ -40,6 +40,20 @@ struct CostAggArgs {
 // Number of tile shapes of the fused kernel (ids 0 .. kNumTiles-1).
 constexpr int kNumTiles = 6;
 int costagg_pick(const CostAggArgs &a, int nsm);
+bool costagg_fits(const CostAggArgs &a, int tile);
+
+// A batch of frames for the persistent form of the fused kernel.
+constexpr int kMaxBatch = 32;
+struct BatchArgs {
+    int njobs;
+    int total_tiles;                  // filled by the launcher
+    int tile_start[kMaxBatch + 1];    // first tile of each job (filled by the launcher)
+    int nstrip[kMaxBatch];            // strips per job (filled by the launcher)
+    CostAggArgs job[kMaxBatch];       // every job's err points at the same word
+    uint32_t *counter;                // tile counter, zeroed by the launcher
+};
+// Launches the persistent batch kernel with tile shape `tile` on nsm CTAs.
+cudaError_t launch_costagg_batch(BatchArgs &b, int tile, int nsm, cudaStream_t s);
 
 // Launchers (each returns the launch error, cudaSuccess on success).
 cudaError_t launch_grey(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t *g_l, uint8_t *g_r,

@@ -6,9 +6,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
+#include <vector>
 
 using namespace stereo;
 
@@ -68,6 +71,16 @@ struct stereo_ctx {
     int prof_next = 0;
     double prof_acc[STEREO_NUM_STAGES] = {};
     int prof_n = 0;
+
+    // Batched frames: their own workspace, the graph of the last batch and
+    // the autotuner's choices of tile shape per batch signature.
+    void *bws = nullptr;
+    size_t bws_size = 0;
+    cudaGraphExec_t bexec = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    std::map<std::string, int> tune;
+    int last_batch_tile = -1;
+    float last_batch_tune_ms[kNumTiles] = {};
 };
 
 namespace {
@@ -368,6 +381,18 @@ int stereo_create(stereo_ctx **out, int device, const stereo_params *p, size_t m
         stereo_destroy(c);
         return STEREO_ECUDA;
     }
+    for (cudaEvent_t *ev : {&c->ev_in, &c->ev_out})
+        if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) {
+            cudaGetLastError();
+            stereo_destroy(c);
+            return STEREO_ECUDA;
+        }
+    for (cudaEvent_t *ev : {&c->ev_t0, &c->ev_t1})
+        if ((e = cudaEventCreate(ev)) != cudaSuccess) {
+            cudaGetLastError();
+            stereo_destroy(c);
+            return STEREO_ECUDA;
+        }
     *out = c;
     return STEREO_OK;
 }
@@ -382,6 +407,10 @@ void stereo_destroy(stereo_ctx *c)
             for (auto &ev : sl.ev)
                 if (ev) cudaEventDestroy(ev);
         if (c->ws) cudaFree(c->ws);
+        if (c->bws) cudaFree(c->bws);
+        if (c->bexec) cudaGraphExecDestroy(c->bexec);
+        for (cudaEvent_t ev : {c->ev_in, c->ev_out, c->ev_t0, c->ev_t1})
+            if (ev) cudaEventDestroy(ev);
         if (c->d_lut) cudaFree(c->d_lut);
         if (c->d_err) cudaFree(c->d_err);
         if (c->h_err) cudaFreeHost(c->h_err);
@@ -563,6 +592,318 @@ int stereo_get_tile(stereo_ctx *c, int W, int H, int Dmax)
     a.wx = c->p.wx;
     a.wy = c->p.wy;
     return costagg_pick(a, c->num_sms);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+
+namespace {
+
+// Device workspace of one frame of a batch.
+struct FrameWs {
+    int W, H, Dmax, X, Y, D;
+    uint8_t *gf[2], *gs[2];
+    uint32_t *pix[2], *arm[2], *armc[2], *key[2];
+    uint8_t *dm;
+    float *dplus;
+};
+
+size_t frame_layout(const stereo_params &p, int W, int H, int Dmax, char *base, FrameWs *f)
+{
+    const bool ds = p.downscale != 0;
+    const int X = ds ? W / 2 : W, Y = ds ? H / 2 : H;
+    const size_t nf = (size_t)W * H, nl = (size_t)X * Y;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *q = base ? base + off : nullptr;
+        off += align256(bytes);
+        return q;
+    };
+    FrameWs g{};
+    g.W = W;
+    g.H = H;
+    g.Dmax = Dmax;
+    g.X = X;
+    g.Y = Y;
+    g.D = ds ? (Dmax + 1) / 2 : Dmax;
+    for (int i = 0; i < 2; ++i) g.gf[i] = (uint8_t *)take(nf);
+    for (int i = 0; i < 2; ++i) g.gs[i] = ds ? (uint8_t *)take(nl) : g.gf[i];
+    for (int i = 0; i < 2; ++i) g.pix[i] = (uint32_t *)take(nl * 4);
+    for (int i = 0; i < 2; ++i) g.arm[i] = (uint32_t *)take(nl * 4);
+    for (int i = 0; i < 2; ++i) g.armc[i] = (uint32_t *)take((size_t)X * (Y + p.wy) * 4);
+    for (int i = 0; i < 2; ++i) g.key[i] = (uint32_t *)take(nl * 4);
+    g.dm = (uint8_t *)take(nl);
+    g.dplus = (float *)take(nl * 4);
+    if (f) *f = g;
+    return off;
+}
+
+CostAggArgs frame_args(const stereo_ctx *c, const FrameWs &f)
+{
+    CostAggArgs a{};
+    a.pix_l = f.pix[0];
+    a.pix_r = f.pix[1];
+    a.arm_l = f.arm[0];
+    a.arm_r = f.arm[1];
+    a.armc_l = f.armc[0];
+    a.armc_r = f.armc[1];
+    a.key_l = f.key[0];
+    a.key_r = f.key[1];
+    a.lut_ad = c->d_lut;
+    a.lut_mc = c->d_lut + 256;
+    a.err = c->d_err;
+    a.wait_limit = c->wait_limit;
+    a.X = f.X;
+    a.Y = f.Y;
+    a.D = f.D;
+    a.wx = c->p.wx;
+    a.wy = c->p.wy;
+    a.P = c->P;
+    a.tile = -1;
+    a.num_sms = c->num_sms;
+    return a;
+}
+
+cudaError_t batch_prep(stereo_ctx *c, const stereo_job &j, const FrameWs &f, cudaStream_t s, int &launches)
+{
+    cudaError_t e = launch_grey(j.left_rgb, j.right_rgb, f.gf[0], f.gf[1], f.W, f.H, s);
+    launches++;
+    if (e == cudaSuccess && c->p.downscale) {
+        e = launch_downscale(f.gf[0], f.gf[1], f.gs[0], f.gs[1], f.W, f.H, s);
+        launches++;
+    }
+    if (e == cudaSuccess) {
+        e = launch_support(f.gs[0], f.gs[1], f.pix[0], f.pix[1], f.arm[0], f.arm[1], f.armc[0], f.armc[1],
+                           f.key[0], f.key[1], c->d_err, f.X, f.Y, c->p.wx, c->p.wy, c->p.tc, s);
+        launches += 2;
+    }
+    return e;
+}
+
+cudaError_t batch_post(stereo_ctx *c, const stereo_job &j, const FrameWs &f, cudaStream_t s, int &launches)
+{
+    float *dplus = c->p.downscale ? f.dplus : j.disp_out;
+    cudaError_t e = launch_refine(f.key[0], f.key[1], f.gs[0], f.X, f.Y, c->p.t_fill, j.dl_out, j.dr_out,
+                                  j.gcp_out, f.dm, dplus, s);
+    launches++;
+    if (e == cudaSuccess && c->p.downscale) {
+        e = launch_upscale(dplus, f.gs[0], f.gf[0], f.X, f.Y, f.W, f.H, c->p.t_fill, j.disp_out, s);
+        launches++;
+    }
+    return e;
+}
+
+std::string batch_signature(const stereo_ctx *c, const std::vector<FrameWs> &fw)
+{
+    char buf[512];
+    cudaDeviceProp prop;
+    const char *name = cudaGetDeviceProperties(&prop, c->device) == cudaSuccess ? prop.name : "gpu";
+    snprintf(buf, sizeof buf, "%.200s sms%d wx%d wy%d scale%d ds%d |", name, c->num_sms, c->p.wx, c->p.wy,
+             c->p.cost_scale, c->p.downscale);
+    std::string sig = buf;
+    std::vector<std::string> parts;
+    for (const FrameWs &f : fw) {
+        snprintf(buf, sizeof buf, " %dx%dx%d", f.X, f.Y, f.D);
+        parts.push_back(buf);
+    }
+    std::sort(parts.begin(), parts.end());
+    for (const std::string &q : parts) sig += q;
+    for (char &ch : sig)
+        if (ch == '\t' || ch == '\n') ch = ' ';
+    return sig;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stereo_compute_batch(stereo_ctx *c, int n, const stereo_job *jobs, void *stream)
+{
+    if (!c) return STEREO_EINVAL;
+    c->err.clear();
+    if (n < 1 || n > kMaxBatch || !jobs) return fail(c, STEREO_EINVAL, "batch size must be in [1, %d]", kMaxBatch);
+    for (int i = 0; i < n; ++i) {
+        int rc = check_frame(c, jobs[i].left_rgb, jobs[i].right_rgb, jobs[i].W, jobs[i].H, jobs[i].Dmax,
+                             jobs[i].disp_out);
+        if (rc != STEREO_OK) return fail(c, rc, "job %d: %s", i, c->err.c_str());
+    }
+    DeviceGuard g(c->device);
+
+    // jobs largest first, so the persistent kernel starts the long sweeps early
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto work = [&](int i) {
+        const stereo_job &j = jobs[i];
+        const double X = c->p.downscale ? j.W / 2 : j.W, Y = c->p.downscale ? j.H / 2 : j.H;
+        const double D = c->p.downscale ? (j.Dmax + 1) / 2 : j.Dmax;
+        return X * Y * D;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+
+    // workspace: one frame layout per job plus the tile counter
+    std::vector<size_t> offs(n);
+    size_t need = 256;
+    for (int k = 0; k < n; ++k) {
+        const stereo_job &j = jobs[order[k]];
+        offs[k] = need;
+        need += frame_layout(c->p, j.W, j.H, j.Dmax, nullptr, nullptr);
+    }
+    if (need > c->bws_size) {
+        if (c->mem_cap && need + c->ws_size > c->mem_cap)
+            return fail(c, STEREO_ENOMEM, "batch workspace of %zu bytes exceeds the cap", need);
+        if (c->bws) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->bws);
+            c->bws = nullptr;
+            c->bws_size = 0;
+        }
+        if (cudaMalloc(&c->bws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, STEREO_ENOMEM, "cudaMalloc(%zu) for the batch failed", need);
+        }
+        c->bws_size = need;
+    }
+    std::vector<FrameWs> fw(n);
+    BatchArgs b{};
+    b.njobs = n;
+    b.counter = (uint32_t *)c->bws;
+    for (int k = 0; k < n; ++k) {
+        const stereo_job &j = jobs[order[k]];
+        frame_layout(c->p, j.W, j.H, j.Dmax, (char *)c->bws + offs[k], &fw[k]);
+        b.job[k] = frame_args(c, fw[k]);
+    }
+    cudaStream_t us = stream ? (cudaStream_t)stream : c->stream;
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    if (us != s) {
+        if ((e = cudaEventRecord(c->ev_in, us)) != cudaSuccess || (e = cudaStreamWaitEvent(s, c->ev_in, 0)) != cudaSuccess)
+            return cuda_fail(c, e, "stream ordering");
+    }
+
+    // tile shape: fixed, remembered for this batch signature, or tuned now
+    int tile = c->tile;
+    int launches = 0;
+    if (tile >= 0) {
+        for (int k = 0; k < n; ++k)
+            if (!costagg_fits(b.job[k], tile)) return fail(c, STEREO_EINVAL, "tile %d does not fit job %d", tile, k);
+    } else {
+        const std::string sig = batch_signature(c, fw);
+        auto it = c->tune.find(sig);
+        if (it != c->tune.end()) {
+            tile = it->second;
+        } else {
+            // the autotuner: run the preparation once, then time each tile
+            // shape that fits every job (one warm-up and two timed launches)
+            for (int k = 0; k < n; ++k)
+                if ((e = batch_prep(c, jobs[order[k]], fw[k], s, launches)) != cudaSuccess)
+                    return cuda_fail(c, e, "kernel launch");
+            float best = 0.f;
+            for (int t = 0; t < kNumTiles; ++t) {
+                c->last_batch_tune_ms[t] = -1.f;
+                bool ok = true;
+                for (int k = 0; k < n && ok; ++k) ok = costagg_fits(b.job[k], t);
+                if (!ok) continue;
+                float tmin = 0.f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    BatchArgs bt = b;
+                    if ((e = cudaEventRecord(c->ev_t0, s)) != cudaSuccess ||
+                        (e = launch_costagg_batch(bt, t, c->num_sms, s)) != cudaSuccess ||
+                        (e = cudaEventRecord(c->ev_t1, s)) != cudaSuccess ||
+                        (e = cudaEventSynchronize(c->ev_t1)) != cudaSuccess)
+                        return cuda_fail(c, e, "autotune");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1);
+                    if (rep == 1 || (rep > 1 && ms < tmin)) tmin = ms;
+                }
+                c->last_batch_tune_ms[t] = tmin;
+                if (tile < 0 || tmin < best) {
+                    best = tmin;
+                    tile = t;
+                }
+            }
+            if (tile < 0) return fail(c, STEREO_EINVAL, "no tile shape fits every job of the batch");
+            c->tune[sig] = tile;
+        }
+    }
+
+    // capture the batch as one graph, then update the last graph in place
+    launches = 0;
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(c, e, "stream capture");
+    for (int k = 0; k < n && e == cudaSuccess; ++k) e = batch_prep(c, jobs[order[k]], fw[k], s, launches);
+    if (e == cudaSuccess) {
+        e = launch_costagg_batch(b, tile, c->num_sms, s);
+        launches++;
+    }
+    for (int k = 0; k < n && e == cudaSuccess; ++k) e = batch_post(c, jobs[order[k]], fw[k], s, launches);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return cuda_fail(c, e != cudaSuccess ? e : e2, "batch capture");
+    }
+    if (c->bexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->bexec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->bexec);
+            c->bexec = nullptr;
+        }
+    }
+    if (!c->bexec && (e = cudaGraphInstantiate(&c->bexec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        c->bexec = nullptr;
+        return cuda_fail(c, e, "graph instantiate");
+    }
+    cudaGraphDestroy(graph);
+    if ((e = cudaGraphLaunch(c->bexec, s)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    if (us != s) {
+        if ((e = cudaEventRecord(c->ev_out, s)) != cudaSuccess || (e = cudaStreamWaitEvent(us, c->ev_out, 0)) != cudaSuccess)
+            return cuda_fail(c, e, "stream ordering");
+    }
+    c->launches = launches;
+    c->last_batch_tile = tile;
+    return STEREO_OK;
+}
+
+int stereo_batch_tile(const stereo_ctx *c, float *tune_ms, int n)
+{
+    if (!c) return STEREO_EINVAL;
+    if (tune_ms)
+        for (int i = 0; i < n && i < kNumTiles; ++i) tune_ms[i] = c->last_batch_tune_ms[i];
+    return c->last_batch_tile;
+}
+
+int stereo_tune_save(stereo_ctx *c, const char *path)
+{
+    if (!c || !path) return STEREO_EINVAL;
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(c, STEREO_EINVAL, "cannot write %s", path);
+    for (const auto &kv : c->tune) fprintf(f, "%s\t%d\n", kv.first.c_str(), kv.second);
+    fclose(f);
+    return (int)c->tune.size();
+}
+
+int stereo_tune_load(stereo_ctx *c, const char *path)
+{
+    if (!c || !path) return STEREO_EINVAL;
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(c, STEREO_EINVAL, "cannot read %s", path);
+    char line[1024];
+    int n = 0;
+    while (fgets(line, sizeof line, f)) {
+        char *tab = strrchr(line, '\t');
+        if (!tab) continue;
+        *tab = '\0';
+        const int t = atoi(tab + 1);
+        if (t < 0 || t >= kNumTiles) continue;
+        c->tune[line] = t;
+        ++n;
+    }
+    fclose(f);
+    return n;
 }
 
 }  // extern "C"
