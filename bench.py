@@ -182,6 +182,113 @@ def cpu_baseline_leg():
             "sample": f"{n} full 1436x992/145 frames, whole pipeline, single thread"}
 
 
+BATCH_MENU = [(640, 480, 64), (1024, 768, 96), (1436, 992, 145), (1920, 1080, 192)]
+
+
+def measure_batch(dev, stream, steps=20, warmup=3, seed=2):
+    """Batched form: 16 pairs drawn by seed from the menu, one stereo_compute_batch
+    call per step (persistent fused kernel, CUDA graph, autotuned tile)."""
+    import numpy as np
+    import torch
+
+    from paper_2212_00488_gb300 import Stereo, _lib, scenes
+    from paper_2212_00488_gb300.stereo import stream_handle
+    rng = np.random.default_rng(seed)
+    picks = [BATCH_MENU[i] for i in rng.integers(0, len(BATCH_MENU), size=16)]
+    frames = []
+    for shape in sorted(set(picks)):
+        W, H, dmax = shape
+        pool = scenes.scene_pool(W, H, dmax, 12, seed, picks.count(shape))
+        for sc in pool:
+            frames.append((torch.from_numpy(sc.left).to(dev), torch.from_numpy(sc.right).to(dev), W, H, dmax))
+    outs = [torch.empty((H, W), dtype=torch.float32, device=dev) for _, _, W, H, _ in frames]
+    jobs = [_lib.stereo_job(lt.data_ptr(), rt.data_ptr(), W, H, dmax, o.data_ptr(), None, None, None)
+            for (lt, rt, W, H, dmax), o in zip(frames, outs)]
+    st = Stereo(dev.index)
+    h = stream_handle(stream)
+    for _ in range(warmup):
+        _lib.stereo_compute_batch(st.ctx, jobs, h)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        _lib.stereo_compute_batch(st.ctx, jobs, h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _lib.stereo_sync(st.ctx)
+    ms = e0.elapsed_time(e1) / steps
+    tile, tune_ms = _lib.stereo_batch_tile(st.ctx)
+    launches = _lib.stereo_last_launch_count(st.ctx)
+    st.close()
+    whd = sum(W * H * dmax for _, _, W, H, dmax in frames)
+    return {"workload": "16 pairs drawn by seed from 640x480/64, 1024x768/96, 1436x992/145, 1920x1080/192",
+            "shapes": [list(p) for p in picks], "value": 16 / (ms / 1e3), "unit": "frames/s",
+            "mde_per_s": whd / (ms / 1e3), "ms_per_batch": ms, "steps": steps, "warmup": warmup,
+            "tile": tile, "autotune_ms": [round(t, 4) for t in tune_ms], "gpu_launches_per_batch": launches}
+
+
+SERVE_MENU = [(640, 480, 64), (1436, 992, 145), (1920, 1080, 192)]
+
+
+def measure_serve(dev, seconds=10.0, rate=120.0, seed=4):
+    """Serving form: Poisson arrivals at `rate` per second for `seconds`, each a
+    single pair of a resolution drawn uniformly from the menu, device-resident
+    inputs, continuous batching with an 8 GB admission cap."""
+    import numpy as np
+    import torch
+
+    from paper_2212_00488_gb300 import scenes
+    from paper_2212_00488_gb300.serve import StereoServer
+    rng = np.random.default_rng(seed)
+    pool = []
+    for W, H, dmax in SERVE_MENU:
+        for sc in scenes.scene_pool(W, H, dmax, 12, seed, 2):
+            pool.append((torch.from_numpy(sc.left).to(dev), torch.from_numpy(sc.right).to(dev), W, H, dmax))
+    torch.cuda.synchronize()
+    # one autotuning run on the largest frame of the menu picks the tile shape
+    # the server then keeps, so no request pays for tuning
+    from paper_2212_00488_gb300 import Stereo, _lib
+    from paper_2212_00488_gb300.stereo import stream_handle
+    lt, rt, W, H, dmax = pool[-1]
+    tuner = Stereo(dev.index)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    _lib.stereo_compute_batch(tuner.ctx, [_lib.stereo_job(lt.data_ptr(), rt.data_ptr(), W, H, dmax, out.data_ptr(),
+                                                          None, None, None)],
+                              stream_handle(torch.cuda.current_stream(dev)))
+    torch.cuda.synchronize()
+    tile, _ = _lib.stereo_batch_tile(tuner.ctx)
+    tuner.close()
+    srv = StereoServer(dev.index, mem_cap_bytes=8 << 30, lanes=2, max_batch=16, tile=tile)
+    for lt, rt, _, _, dmax in pool:                # warm-up: graphs, autotuning
+        srv.submit(lt, rt, dmax).result(timeout=120)
+    srv.latencies.clear()
+    done0 = srv.completed
+    futs, whd = [], 0
+    t0 = time.perf_counter()
+    t_next = t0
+    while True:
+        t_next += rng.exponential(1.0 / rate)
+        if t_next - t0 > seconds:
+            break
+        delay = t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        lt, rt, W, H, dmax = pool[2 * int(rng.integers(0, len(SERVE_MENU))) + int(rng.integers(0, 2))]
+        futs.append(srv.submit(lt, rt, dmax))
+        whd += W * H * dmax
+    for f in futs:
+        f.result(timeout=120)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    n = st["completed"] - done0
+    return {"workload": f"Poisson {rate:.0f} req/s for {seconds:.0f} s, single pairs from "
+                        "640x480/64, 1436x992/145, 1920x1080/192, device-resident, 8 GB admission cap",
+            "requests": n, "value": n / wall, "unit": "frames/s", "mde_per_s": whd / wall,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "batches": st["batches"],
+            "peak_admitted_bytes": st["peak_admitted_bytes"], "seconds": wall, "tile": tile}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -299,6 +406,9 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
         }
+        if not args.no_forms:
+            line["forms"] = {"batch": measure_batch(dev, stream),
+                             "serve": measure_serve(dev, seconds=args.serve_seconds)}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
         print(json.dumps(line), flush=True)
@@ -314,6 +424,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched/served/differentiable forms")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served request stream")
     ap.add_argument("--tile", type=int, default=-1, help="force a tile shape of the fused kernel (-1: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:

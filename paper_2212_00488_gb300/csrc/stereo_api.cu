@@ -76,7 +76,7 @@ struct stereo_ctx {
     // the autotuner's choices of tile shape per batch signature.
     void *bws = nullptr;
     size_t bws_size = 0;
-    cudaGraphExec_t bexec = nullptr;
+    std::map<int, cudaGraphExec_t> bexec;   // one graph per batch size, updated in place
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
     std::map<std::string, int> tune;
     int last_batch_tile = -1;
@@ -408,7 +408,7 @@ void stereo_destroy(stereo_ctx *c)
                 if (ev) cudaEventDestroy(ev);
         if (c->ws) cudaFree(c->ws);
         if (c->bws) cudaFree(c->bws);
-        if (c->bexec) cudaGraphExecDestroy(c->bexec);
+        for (auto &kv : c->bexec) cudaGraphExecDestroy(kv.second);
         for (cudaEvent_t ev : {c->ev_in, c->ev_out, c->ev_t0, c->ev_t1})
             if (ev) cudaEventDestroy(ev);
         if (c->d_lut) cudaFree(c->d_lut);
@@ -844,21 +844,24 @@ int stereo_compute_batch(stereo_ctx *c, int n, const stereo_job *jobs, void *str
         cudaGetLastError();
         return cuda_fail(c, e != cudaSuccess ? e : e2, "batch capture");
     }
-    if (c->bexec) {
+    // batches of one size share the graph topology, so the last graph of that
+    // size is updated in place; a new size or tile shape instantiates anew
+    cudaGraphExec_t &exec = c->bexec[n];
+    if (exec) {
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(c->bexec, graph, &info) != cudaSuccess) {
+        if (cudaGraphExecUpdate(exec, graph, &info) != cudaSuccess) {
             cudaGetLastError();
-            cudaGraphExecDestroy(c->bexec);
-            c->bexec = nullptr;
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
         }
     }
-    if (!c->bexec && (e = cudaGraphInstantiate(&c->bexec, graph, 0)) != cudaSuccess) {
+    if (!exec && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
         cudaGraphDestroy(graph);
-        c->bexec = nullptr;
+        exec = nullptr;
         return cuda_fail(c, e, "graph instantiate");
     }
     cudaGraphDestroy(graph);
-    if ((e = cudaGraphLaunch(c->bexec, s)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
     if (us != s) {
         if ((e = cudaEventRecord(c->ev_out, s)) != cudaSuccess || (e = cudaStreamWaitEvent(us, c->ev_out, 0)) != cudaSuccess)
             return cuda_fail(c, e, "stream ordering");
