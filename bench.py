@@ -289,6 +289,49 @@ def measure_serve(dev, seconds=10.0, rate=120.0, seed=4):
             "peak_admitted_bytes": st["peak_admitted_bytes"], "seconds": wall, "tile": tile}
 
 
+def measure_diff(dev, steps=5, warmup=2, seed=6):
+    """Differentiable form: a batch of 4 pairs of 718x496 (FP32 on [0, 1]),
+    73 disparities, soft-argmin at temperature 0.1, L1 loss to the known
+    disparity, forward and backward through the cross aggregation."""
+    import numpy as np
+    import torch
+
+    from paper_2212_00488_gb300 import Stereo
+    from paper_2212_00488_gb300.diff import soft_argmin_disparity
+    from paper_2212_00488_gb300 import scenes
+    W, H, D, B = 718, 496, 73, 4
+    sc = [scenes.make_scene(W, H, D, planes=40, seed=seed + b) for b in range(B)]
+    UL = torch.from_numpy(np.stack([s.left for s in sc])).to(dev)
+    UR = torch.from_numpy(np.stack([s.right for s in sc])).to(dev)
+    L = (UL.float() / 255.0).contiguous().requires_grad_(True)
+    R = (UR.float() / 255.0).contiguous().requires_grad_(True)
+    GT = torch.from_numpy(np.stack([s.disp for s in sc]).astype(np.float32)).to(dev)
+    T = torch.tensor([1.0, 1.0, 0.3, 2.3], device=dev, requires_grad=True)
+    st = Stereo(dev.index, downscale=0)
+
+    def step():
+        dh = soft_argmin_disparity(L, R, T, UL, UR, D, 0.1, st)
+        loss = (dh - GT).abs().mean()
+        loss.backward()
+        return loss
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        loss = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st.close()
+    return {"workload": "4 pairs 718x496 FP32, D 73, soft-argmin tau 0.1, L1 loss, forward + backward",
+            "value": B / (ms / 1e3), "unit": "pairs/s (forward + backward)", "ms_per_step": ms,
+            "mde_per_s": B * W * H * D / (ms / 1e3), "loss": float(loss.item()),
+            "grad_theta": [float(v) for v in T.grad.cpu()], "steps": steps, "warmup": warmup}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -408,7 +451,8 @@ def run_ours(args):
         }
         if not args.no_forms:
             line["forms"] = {"batch": measure_batch(dev, stream),
-                             "serve": measure_serve(dev, seconds=args.serve_seconds)}
+                             "serve": measure_serve(dev, seconds=args.serve_seconds),
+                             "diff": measure_diff(dev)}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
         print(json.dumps(line), flush=True)

@@ -220,6 +220,40 @@ STEREO_API int stereo_tune_save(stereo_ctx *ctx, const char *path);
  * were read or EINVAL. */
 STEREO_API int stereo_tune_load(stereo_ctx *ctx, const char *path);
 
+/* Differentiable form (a training form of the method; the paper has only the
+ * forward WTA). Left base, processed resolution W x H (no downscaling),
+ * D disparities, B pairs. Per pair, in FP32:
+ *   g        = (77 R + 150 G + 29 B) / 256 of the float RGB on [0, 1]
+ *   C        = w_AD (1 - exp(-|gL(x,y) - gR(x-d,y)| / l_AD))
+ *            + w_MC (1 - exp(-MC(x,y,d) / l_MC))  (Eqs. 3-5), the constant
+ *              w_AD (1 - exp(-1/l_AD)) + w_MC (1 - exp(-6/l_MC)) when x < d
+ *   CA       = the cross aggregation of Eqs. 7-8 divided by the support size
+ *   dhat     = sum_d d softmax_d(-CA(x,y,d) / tau)
+ * The census codes MC and the arms are frozen: they come from the uint8
+ * images left_u8 / right_u8 through the integer path (grey, census, arms with
+ * the context's tc, wx, wy) and are not differentiated.
+ *  left, right: device float [B][H][W][3]; left_u8, right_u8: device uint8
+ *    [B][H][W][3]; theta: device float [4] = (w_AD, w_MC, l_AD, l_MC).
+ *  dhat: device float [B][H][W] out; stats: device float [B][H][W][2] out
+ *    (softmax maximum and sum per pixel, needed by the backward).
+ * H up to 8192, W up to 4096, D up to 256, B up to 64. Asynchronous. */
+STEREO_API int stereo_diff_forward(stereo_ctx *ctx, int B, int W, int H, int D, const float *left,
+                                   const float *right, const uint8_t *left_u8, const uint8_t *right_u8,
+                                   const float *theta, float tau, float *dhat, float *stats, void *stream);
+
+/* Backward of stereo_diff_forward for the incoming gradient grad_dhat
+ * (device float [B][H][W]): writes the gradients of sum(grad_dhat * dhat)
+ * for left and right (device float [B][H][W][3], overwritten) and theta
+ * (device float [4], overwritten). The aggregated cost is recomputed a slab
+ * of disparities at a time, never stored; the adjoint of the aggregation is
+ * the same arm sums transposed over the frozen supports. dhat and stats must
+ * be the forward's outputs for the same inputs. Deterministic. */
+STEREO_API int stereo_diff_backward(stereo_ctx *ctx, int B, int W, int H, int D, const float *left,
+                                    const float *right, const uint8_t *left_u8, const uint8_t *right_u8,
+                                    const float *theta, float tau, const float *dhat, const float *stats,
+                                    const float *grad_dhat, float *grad_left, float *grad_right,
+                                    float *grad_theta, void *stream);
+
 /* stereo_compute without any allocation at call time. The paper has no
  * counterpart: this entry point exists for callers that must not allocate
  * device memory while they run, such as a real-time frame loop that may not

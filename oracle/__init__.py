@@ -53,6 +53,10 @@ def lib():
         L.oracle_median3.argtypes = [_u8p, _int, _int, _u8p]
         L.oracle_fill.argtypes = [_u8p, _u8p, _u8p, _int, _int, _int, _f32p]
         L.oracle_upscale.argtypes = [_f32p, _u8p, _u8p, _int, _int, _int, _int, _int, _f32p]
+        L.oracle_diff.argtypes = [_f64p, _f64p] + [_u8p] * 6 + [_int] * 3 + [_f64p, _dbl, _f64p,
+                                                                           ctypes.c_void_p, ctypes.c_void_p,
+                                                                           ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_diff.restype = _int
         _lib = L
     return _lib
 
@@ -236,3 +240,41 @@ def pipeline(left_rgb, right_rgb, dmax: int, p: Params = Params()) -> Result:
     else:
         disp = dplus.copy()
     return Result(disp, dl, dr, gcp, dm, dplus, gl, gr, cl, cr, al, ar, gl_full)
+
+
+def grey_f(rgb):
+    """Grey on [0, 1] of float RGB on [0, 1]: the integer path's BT.601 weights
+    (77, 150, 29) / 256 without rounding."""
+    rgb = np.asarray(rgb, np.float64)
+    return (77.0 * rgb[..., 0] + 150.0 * rgb[..., 1] + 29.0 * rgb[..., 2]) / 256.0
+
+
+def quantise(g):
+    """The uint8 grey the frozen census codes and arms are computed from."""
+    return np.clip(np.rint(np.asarray(g, np.float64) * 255.0), 0, 255).astype(np.uint8)
+
+
+def diff_forward_backward(gL, gR, census_l, census_r, arms_l, D, theta, tau=0.1, go=None):
+    """Differentiable form (FP64, left base): soft-argmin disparity and, when go
+    is given, the gradient of sum(go * dhat) for gL, gR and theta
+    (w_AD, w_MC, lambda_AD, lambda_MC). Arms and census codes are frozen."""
+    gL = _c(gL, np.float64)
+    gR = _c(gR, np.float64)
+    Y, X = gL.shape
+    th = _c(theta, np.float64)
+    dhat = np.empty((Y, X), np.float64)
+    hm, hp, vm, vp = (_c(a, np.uint8) for a in arms_l)
+    args = [gL, gR, _c(census_l, np.uint8), _c(census_r, np.uint8), hm, hp, vm, vp, X, Y, D, th, tau, dhat]
+    if go is None:
+        rc = lib().oracle_diff(*args, None, None, None, None)
+        if rc != 0:
+            raise MemoryError("oracle_diff")
+        return dhat
+    go = _c(go, np.float64)
+    g_l = np.empty((Y, X), np.float64)
+    g_r = np.empty((Y, X), np.float64)
+    g_t = np.empty(4, np.float64)
+    rc = lib().oracle_diff(*args, go.ctypes.data, g_l.ctypes.data, g_r.ctypes.data, g_t.ctypes.data)
+    if rc != 0:
+        raise MemoryError("oracle_diff")
+    return dhat, g_l, g_r, g_t

@@ -409,3 +409,135 @@ void oracle_upscale(const float *dp, const uint8_t *gs, const uint8_t *gf, int X
             out[(size_t)Yo * W + Xo] = v;
         }
 }
+
+/* ------------------------------------------------------------------------
+ * Differentiable form, FP64 (test infrastructure like the rest of the file).
+ * Left base only. Intensities gL, gR are grey values on [0, 1]; the census
+ * codes and the arms are frozen inputs (computed from the quantised images),
+ * so the only non-smooth steps are |.| and the comparisons they freeze.
+ *   C(x,y,d)  = w_AD (1 - exp(-|gL(x,y) - gR(x-d,y)| / l_AD))
+ *             + w_MC (1 - exp(-MC / l_MC))            (Eqs. 3-5)
+ *             = P = w_AD (1 - exp(-1/l_AD)) + w_MC (1 - exp(-6/l_MC)) if x < d
+ *   CA        = aggregation of Eqs. 7-8 over the frozen arms, divided by the
+ *               support size n(x,y) (constant over d, so the WTA of Eq. 9 is
+ *               unchanged; it keeps the soft-argmin's inputs of order one)
+ *   p_d       = softmax over d of -CA(x,y,d) / tau
+ *   dhat(x,y) = sum_d d p_d
+ * theta = (w_AD, w_MC, l_AD, l_MC). With go != NULL the gradient of
+ * sum(go * dhat) is returned for gL, gR and theta: the aggregation's adjoint
+ * is written as plain scatters over each anchor's support.
+ * ------------------------------------------------------------------------ */
+int oracle_diff(const double *gL, const double *gR, const uint8_t *cL, const uint8_t *cR,
+                const uint8_t *hm, const uint8_t *hp, const uint8_t *vm, const uint8_t *vp,
+                int X, int Y, int D, const double *theta, double tau, double *dhat,
+                const double *go, double *g_gL, double *g_gR, double *g_theta)
+{
+    const double wad = theta[0], wmc = theta[1], lad = theta[2], lmc = theta[3];
+    const size_t n = (size_t)X * Y, nv = n * (size_t)D;
+    double *C = malloc(nv * sizeof *C), *Z = malloc(nv * sizeof *Z), *CAx = malloc(n * sizeof *CAx);
+    double *ns = malloc(n * sizeof *ns);
+    if (!C || !Z || !CAx || !ns) { free(C); free(Z); free(CAx); free(ns); return -1; }
+    const double P = wad * (1.0 - exp(-1.0 / lad)) + wmc * (1.0 - exp(-6.0 / lmc));
+    for (int y = 0; y < Y; ++y)
+        for (int x = 0; x < X; ++x) {
+            size_t i = (size_t)y * X + x;
+            double s = 0;
+            for (int t = -(int)vm[i]; t <= (int)vp[i]; ++t) {
+                size_t k = (size_t)(y + t) * X + x;
+                s += (double)hm[k] + (double)hp[k] + 1.0;
+            }
+            ns[i] = s;
+        }
+    for (int d = 0; d < D; ++d) {
+        double *Cd = C + (size_t)d * n, *Zd = Z + (size_t)d * n;
+        for (int y = 0; y < Y; ++y)
+            for (int x = 0; x < X; ++x) {
+                size_t i = (size_t)y * X + x;
+                if (x - d < 0) { Cd[i] = P; continue; }
+                double a = fabs(gL[i] - gR[i - d]);
+                int h = popcount6(cL[i] ^ cR[i - d]);
+                Cd[i] = wad * (1.0 - exp(-a / lad)) + wmc * (1.0 - exp(-(double)h / lmc));
+            }
+        for (int y = 0; y < Y; ++y)
+            for (int x = 0; x < X; ++x) {
+                size_t i = (size_t)y * X + x;
+                double s = 0;
+                for (int t = -(int)hm[i]; t <= (int)hp[i]; ++t) s += Cd[i + t];
+                CAx[i] = s;
+            }
+        for (int y = 0; y < Y; ++y)
+            for (int x = 0; x < X; ++x) {
+                size_t i = (size_t)y * X + x;
+                double s = 0;
+                for (int t = -(int)vm[i]; t <= (int)vp[i]; ++t) s += CAx[(size_t)(y + t) * X + x];
+                Zd[i] = -(s / ns[i]) / tau;
+            }
+    }
+    /* softmax over d and the expected disparity; Z becomes p */
+    for (size_t i = 0; i < n; ++i) {
+        double m = -INFINITY;
+        for (int d = 0; d < D; ++d) if (Z[(size_t)d * n + i] > m) m = Z[(size_t)d * n + i];
+        double s = 0;
+        for (int d = 0; d < D; ++d) s += exp(Z[(size_t)d * n + i] - m);
+        double e = 0;
+        for (int d = 0; d < D; ++d) {
+            double p = exp(Z[(size_t)d * n + i] - m) / s;
+            Z[(size_t)d * n + i] = p;
+            e += d * p;
+        }
+        dhat[i] = e;
+    }
+    if (go) {
+        double *G1 = malloc(n * sizeof *G1), *G2 = malloc(n * sizeof *G2), *Gc = malloc(n * sizeof *Gc);
+        if (!G1 || !G2 || !Gc) { free(G1); free(G2); free(Gc); free(C); free(Z); free(CAx); free(ns); return -1; }
+        for (size_t i = 0; i < n; ++i) { g_gL[i] = 0; g_gR[i] = 0; }
+        for (int k = 0; k < 4; ++k) g_theta[k] = 0;
+        for (int d = 0; d < D; ++d) {
+            const double *pd = Z + (size_t)d * n;
+            /* d dhat / d CA(x,y,d) = p_d (d - dhat) * (-1/tau) / n(x,y) */
+            for (size_t i = 0; i < n; ++i) Gc[i] = go[i] * pd[i] * ((double)d - dhat[i]) * (-1.0 / tau) / ns[i];
+            /* adjoint of the vertical sum: each anchor sends its value to its span */
+            for (size_t i = 0; i < n; ++i) G1[i] = 0;
+            for (int y = 0; y < Y; ++y)
+                for (int x = 0; x < X; ++x) {
+                    size_t i = (size_t)y * X + x;
+                    for (int t = -(int)vm[i]; t <= (int)vp[i]; ++t) G1[(size_t)(y + t) * X + x] += Gc[i];
+                }
+            /* adjoint of the horizontal sum: each pixel sends to its own row window */
+            for (size_t i = 0; i < n; ++i) G2[i] = 0;
+            for (int y = 0; y < Y; ++y)
+                for (int x = 0; x < X; ++x) {
+                    size_t i = (size_t)y * X + x;
+                    for (int t = -(int)hm[i]; t <= (int)hp[i]; ++t) G2[i + t] += G1[i];
+                }
+            /* through the cost */
+            for (int y = 0; y < Y; ++y)
+                for (int x = 0; x < X; ++x) {
+                    size_t i = (size_t)y * X + x;
+                    double g = G2[i];
+                    if (x - d < 0) {
+                        double ea = exp(-1.0 / lad), eh = exp(-6.0 / lmc);
+                        g_theta[0] += g * (1.0 - ea);
+                        g_theta[1] += g * (1.0 - eh);
+                        g_theta[2] += g * wad * (-ea * (1.0 / (lad * lad)));
+                        g_theta[3] += g * wmc * (-eh * (6.0 / (lmc * lmc)));
+                        continue;
+                    }
+                    double diff = gL[i] - gR[i - d], a = fabs(diff);
+                    double h = (double)popcount6(cL[i] ^ cR[i - d]);
+                    double ea = exp(-a / lad), eh = exp(-h / lmc);
+                    g_theta[0] += g * (1.0 - ea);
+                    g_theta[1] += g * (1.0 - eh);
+                    g_theta[2] += g * wad * (-ea * (a / (lad * lad)));
+                    g_theta[3] += g * wmc * (-eh * (h / (lmc * lmc)));
+                    double sgn = diff > 0 ? 1.0 : (diff < 0 ? -1.0 : 0.0);
+                    double dCda = wad * ea / lad;
+                    g_gL[i] += g * dCda * sgn;
+                    g_gR[i - d] -= g * dCda * sgn;
+                }
+        }
+        free(G1); free(G2); free(Gc);
+    }
+    free(C); free(Z); free(CAx); free(ns);
+    return 0;
+}

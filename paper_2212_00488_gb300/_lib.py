@@ -79,6 +79,9 @@ _SIGNATURES = {
     "stereo_batch_tile": (_i, [_ctxp, ctypes.POINTER(ctypes.c_float), _i]),
     "stereo_tune_save": (_i, [_ctxp, ctypes.c_char_p]),
     "stereo_tune_load": (_i, [_ctxp, ctypes.c_char_p]),
+    "stereo_diff_forward": (_i, [_ctxp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]),
+    "stereo_diff_backward": (_i, [_ctxp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, _vp]),
     "stereo_compute_noalloc": (_i, [ctypes.POINTER(stereo_params), _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp,
                                     _vp, ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -221,3 +224,15 @@ def stereo_tune_load(ctx, path):
     if rc < 0:
         check(ctx, rc)
     return rc
+
+
+def stereo_diff_forward(ctx, B, W, H, D, left, right, left_u8, right_u8, theta, tau, dhat, stats, stream=0):
+    return check(ctx, load().stereo_diff_forward(ctx, B, W, H, D, left, right, left_u8, right_u8, theta, tau, dhat,
+                                                 stats, stream or None))
+
+
+def stereo_diff_backward(ctx, B, W, H, D, left, right, left_u8, right_u8, theta, tau, dhat, stats, grad_dhat,
+                         grad_left, grad_right, grad_theta, stream=0):
+    return check(ctx, load().stereo_diff_backward(ctx, B, W, H, D, left, right, left_u8, right_u8, theta, tau,
+                                                  dhat, stats, grad_dhat, grad_left, grad_right, grad_theta,
+                                                  stream or None))

@@ -1,0 +1,399 @@
+// Differentiable form of the left-base cost and aggregation (FP32): a soft
+// argmin over the aggregated cost, and its backward as the adjoint of the
+// cross aggregation over the same frozen supports.
+//
+//   g          = (77 R + 150 G + 29 B) / 256 on [0, 1]       (float grey)
+//   census codes and arms: frozen (not differentiated), computed by the
+//              integer path from the pair's uint8 images
+//   C(x,y,d)   = w_AD (1 - exp(-|gL(x,y) - gR(x-d,y)| / l_AD))
+//              + w_MC (1 - exp(-MC / l_MC))                    (Eqs. 3-5)
+//              = P(theta) when x < d
+//   CA(x,y,d)  = Eqs. 7-8 over the frozen arms, divided by the support size
+//   dhat       = sum_d d softmax_d(-CA / tau)
+//
+// The volume is never stored: forward and backward walk the disparities in
+// chunks of kDC, keeping per chunk the x-aggregated slab and, in backward,
+// the slab's gradients. Sums over arms are direct (at most 2 wx + 1 and
+// 2 wy + 1 terms), which keeps FP32 aggregates within about 6e-6 of their
+// exact value. The adjoint gathers for every cell the anchors whose support
+// contains it, so no float atomics are used and results are deterministic.
+#include "internal.cuh"
+
+namespace stereo {
+namespace {
+
+constexpr int kDC = 8;   // disparities per chunk
+__constant__ float kGreyW[3] = {77.f / 256.f, 150.f / 256.f, 29.f / 256.f};
+
+__global__ void diff_grey_kernel(const float *__restrict__ rgb_l, const float *__restrict__ rgb_r,
+                                 float *__restrict__ g_l, float *__restrict__ g_r, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float *rgb = blockIdx.y ? rgb_r : rgb_l;
+    float g = __fmul_rn(kGreyW[0], rgb[3 * i]);
+    g = __fadd_rn(g, __fmul_rn(kGreyW[1], rgb[3 * i + 1]));
+    g = __fadd_rn(g, __fmul_rn(kGreyW[2], rgb[3 * i + 2]));
+    (blockIdx.y ? g_r : g_l)[i] = g;
+}
+
+// Support size n(x,y) = sum over the vertical span of each row's x window.
+__global__ void diff_nsupport_kernel(const uint32_t *__restrict__ arm, int X, int Y, float *__restrict__ ns)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= X * Y) return;
+    const int y = i / X, x = i - y * X;
+    const uint32_t a = arm[i];
+    const int up = (a >> 16) & 0xFF, down = a >> 24;
+    int s = 0;
+    for (int t = -up; t <= down; ++t) {
+        const uint32_t b = arm[(size_t)(y + t) * X + x];
+        s += (int)(b & 0xFF) + (int)((b >> 8) & 0xFF) + 1;
+    }
+    ns[i] = (float)s;
+}
+
+struct Theta {
+    float wad, wmc, lad, lmc;
+};
+
+__device__ __forceinline__ Theta load_theta(const float *t) { return Theta{t[0], t[1], t[2], t[3]}; }
+
+// One block per row y and chunk: the cost row of each disparity of the chunk
+// in shared memory, then each pixel's own x window summed directly.
+__global__ void diff_costx_kernel(const float *__restrict__ gL, const float *__restrict__ gR,
+                                  const uint32_t *__restrict__ pixL, const uint32_t *__restrict__ pixR,
+                                  const uint32_t *__restrict__ arm, const float *__restrict__ theta, int X, int Y,
+                                  int D, int d0, int dc, float *__restrict__ cax)
+{
+    extern __shared__ float crow[];
+    const int y = blockIdx.x;
+    const Theta th = load_theta(theta);
+    const float P = th.wad * (1.f - expf(-1.f / th.lad)) + th.wmc * (1.f - expf(-6.f / th.lmc));
+    const size_t r = (size_t)y * X;
+    for (int k = 0; k < dc && d0 + k < D; ++k) {
+        const int d = d0 + k;
+        __syncthreads();
+        for (int x = threadIdx.x; x < X; x += blockDim.x) {
+            float c = P;
+            if (x >= d) {
+                const float a = fabsf(gL[r + x] - gR[r + x - d]);
+                const int h = __popc((pixL[r + x] ^ pixR[r + x - d]) & 0x3F00u);
+                c = th.wad * (1.f - expf(-a / th.lad)) + th.wmc * (1.f - expf(-(float)h / th.lmc));
+            }
+            crow[x] = c;
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < X; x += blockDim.x) {
+            const uint32_t am = arm[r + x];
+            const int lo = x - (int)(am & 0xFF), hi = x + (int)((am >> 8) & 0xFF);
+            float s = 0.f;
+            for (int t = lo; t <= hi; ++t) s += crow[t];
+            cax[((size_t)k * Y + y) * X + x] = s;
+        }
+    }
+}
+
+__device__ __forceinline__ float vsum(const float *__restrict__ plane, const uint32_t am, int x, int y, int X)
+{
+    const int up = (am >> 16) & 0xFF, down = am >> 24;
+    float s = 0.f;
+    for (int t = -up; t <= down; ++t) s += plane[(size_t)(y + t) * X + x];
+    return s;
+}
+
+// Forward: aggregated cost along y per pixel and an online softmax over d.
+// state = (max z, sum exp(z - max), sum d exp(z - max)) per pixel.
+__global__ void diff_vagg_softmax_kernel(const float *__restrict__ cax, const uint32_t *__restrict__ arm,
+                                         const float *__restrict__ ns, int X, int Y, int D, int d0, int dc,
+                                         float inv_tau, float *__restrict__ state, int first, int last,
+                                         float *__restrict__ dhat, float *__restrict__ stats)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= X * Y) return;
+    const int y = i / X, x = i - y * X;
+    const uint32_t am = arm[i];
+    const float inv_n = 1.f / ns[i];
+    float m = first ? -INFINITY : state[3 * i], s = first ? 0.f : state[3 * i + 1],
+          sd = first ? 0.f : state[3 * i + 2];
+    for (int k = 0; k < dc && d0 + k < D; ++k) {
+        const float z = -(vsum(cax + (size_t)k * X * Y, am, x, y, X) * inv_n) * inv_tau;
+        const float d = (float)(d0 + k);
+        if (z > m) {
+            const float f = expf(m - z);
+            s = s * f + 1.f;
+            sd = sd * f + d;
+            m = z;
+        } else {
+            const float e = expf(z - m);
+            s += e;
+            sd += d * e;
+        }
+    }
+    if (last) {
+        dhat[i] = sd / s;
+        stats[2 * i] = m;
+        stats[2 * i + 1] = s;
+    } else {
+        state[3 * i] = m;
+        state[3 * i + 1] = s;
+        state[3 * i + 2] = sd;
+    }
+}
+
+// Backward 1: d dhat / d CA = p_d (d - dhat) (-1/tau) / n, times the
+// incoming gradient, for the chunk (the aggregated slab is recomputed).
+__global__ void diff_gca_kernel(const float *__restrict__ cax, const uint32_t *__restrict__ arm,
+                                const float *__restrict__ ns, int X, int Y, int D, int d0, int dc, float inv_tau,
+                                const float *__restrict__ dhat, const float *__restrict__ stats,
+                                const float *__restrict__ go, float *__restrict__ g0)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= X * Y) return;
+    const int y = i / X, x = i - y * X;
+    const uint32_t am = arm[i];
+    const float inv_n = 1.f / ns[i];
+    const float m = stats[2 * i], s = stats[2 * i + 1], e = dhat[i], gi = go[i];
+    for (int k = 0; k < dc; ++k) {
+        float v = 0.f;
+        if (d0 + k < D) {
+            const float z = -(vsum(cax + (size_t)k * X * Y, am, x, y, X) * inv_n) * inv_tau;
+            const float p = expf(z - m) / s;
+            v = gi * p * ((float)(d0 + k) - e) * (-inv_tau) * inv_n;
+        }
+        g0[(size_t)k * X * Y + i] = v;
+    }
+}
+
+// Backward 2: adjoint of the vertical sum, gathered: G1(x, y') collects the
+// anchors (x, y) whose vertical span [y - up, y + down] contains y'.
+__global__ void diff_vT_kernel(const float *__restrict__ g0, const uint32_t *__restrict__ arm, int X, int Y,
+                               int wy, int dc, float *__restrict__ g1)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= X * Y) return;
+    const int yp = i / X, x = i - yp * X;
+    const int ya = max(yp - wy, 0), yb = min(yp + wy, Y - 1);
+    for (int k = 0; k < dc; ++k) {
+        const float *plane = g0 + (size_t)k * X * Y;
+        float s = 0.f;
+        for (int y = ya; y <= yb; ++y) {
+            const uint32_t am = arm[(size_t)y * X + x];
+            if (y - (int)((am >> 16) & 0xFF) <= yp && yp <= y + (int)(am >> 24)) s += plane[(size_t)y * X + x];
+        }
+        g1[(size_t)k * X * Y + i] = s;
+    }
+}
+
+// Backward 3: adjoint of the horizontal sum, gathered: G2(x', y) collects the
+// pixels (x, y) whose own window [x - left, x + right] contains x'.
+__global__ void diff_hT_kernel(const float *__restrict__ g1, const uint32_t *__restrict__ arm, int X, int Y,
+                               int wx, int dc, float *__restrict__ g2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= X * Y) return;
+    const int y = i / X, xp = i - y * X;
+    const int xa = max(xp - wx, 0), xb = min(xp + wx, X - 1);
+    const size_t r = (size_t)y * X;
+    for (int k = 0; k < dc; ++k) {
+        const float *plane = g1 + (size_t)k * X * Y;
+        float s = 0.f;
+        for (int x = xa; x <= xb; ++x) {
+            const uint32_t am = arm[r + x];
+            if (x - (int)(am & 0xFF) <= xp && xp <= x + (int)((am >> 8) & 0xFF)) s += plane[r + x];
+        }
+        g2[(size_t)k * X * Y + i] = s;
+    }
+}
+
+// Backward 4: through the cost. Per pixel: its own gradient as the left pixel
+// of every cell (x, y, d), as the right pixel x' of the cells (x' + d, y, d),
+// and its cells' contributions to the four parameters (one partial per block,
+// summed later in a fixed order).
+__global__ void diff_costgrad_kernel(const float *__restrict__ gL, const float *__restrict__ gR,
+                                     const uint32_t *__restrict__ pixL, const uint32_t *__restrict__ pixR,
+                                     const float *__restrict__ theta, int X, int Y, int D, int d0, int dc,
+                                     const float *__restrict__ g2, float *__restrict__ acc_l,
+                                     float *__restrict__ acc_r, float *__restrict__ part)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const Theta th = load_theta(theta);
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    if (i < X * Y) {
+        const int y = i / X, x = i - y * X;
+        const size_t r = (size_t)y * X;
+        float al = 0.f, ar = 0.f;
+        for (int k = 0; k < dc && d0 + k < D; ++k) {
+            const int d = d0 + k;
+            const float *plane = g2 + (size_t)k * X * Y;
+            const float g = plane[i];
+            if (x < d) {
+                const float ea = expf(-1.f / th.lad), eh = expf(-6.f / th.lmc);
+                t0 += g * (1.f - ea);
+                t1 += g * (1.f - eh);
+                t2 += g * th.wad * (-ea / (th.lad * th.lad));
+                t3 += g * th.wmc * (-eh * 6.f / (th.lmc * th.lmc));
+            } else {
+                const float diff = gL[i] - gR[i - d], a = fabsf(diff);
+                const float h = (float)__popc((pixL[i] ^ pixR[i - d]) & 0x3F00u);
+                const float ea = expf(-a / th.lad), eh = expf(-h / th.lmc);
+                t0 += g * (1.f - ea);
+                t1 += g * (1.f - eh);
+                t2 += g * th.wad * (-ea * a / (th.lad * th.lad));
+                t3 += g * th.wmc * (-eh * h / (th.lmc * th.lmc));
+                const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+                al += g * th.wad * ea / th.lad * sgn;
+            }
+            // this pixel as the match of the left pixel x + d
+            if (x + d < X) {
+                const float gg = plane[r + x + d];
+                const float diff = gL[r + x + d] - gR[i], a = fabsf(diff);
+                const float ea = expf(-a / th.lad);
+                const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+                ar -= gg * th.wad * ea / th.lad * sgn;
+            }
+        }
+        acc_l[i] += al;
+        acc_r[i] += ar;
+    }
+    // block partials of the parameter gradients
+    __shared__ float sh[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t0 += __shfl_down_sync(0xffffffffu, t0, o);
+        t1 += __shfl_down_sync(0xffffffffu, t1, o);
+        t2 += __shfl_down_sync(0xffffffffu, t2, o);
+        t3 += __shfl_down_sync(0xffffffffu, t3, o);
+    }
+    if (lane == 0) {
+        sh[0][w] = t0;
+        sh[1][w] = t1;
+        sh[2][w] = t2;
+        sh[3][w] = t3;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float s = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[threadIdx.x][k];
+        part[(size_t)blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+__global__ void diff_finish_kernel(const float *__restrict__ acc_l, const float *__restrict__ acc_r, int n,
+                                   float *__restrict__ grad_l, float *__restrict__ grad_r)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        grad_l[3 * i + c] = acc_l[i] * kGreyW[c];
+        grad_r[3 * i + c] = acc_r[i] * kGreyW[c];
+    }
+}
+
+// Sum of all block partials in one fixed order (double accumulation).
+__global__ void diff_theta_reduce_kernel(const float *__restrict__ part, int nparts, float *__restrict__ grad)
+{
+    const int c = threadIdx.x;
+    if (c >= 4) return;
+    double s = 0.0;
+    for (int k = 0; k < nparts; ++k) s += (double)part[(size_t)k * 4 + c];
+    grad[c] = (float)s;
+}
+
+}  // namespace
+
+constexpr int kDiffNT = 256;
+
+size_t diff_workspace_bytes(int X, int Y, int wy, int B, int D)
+{
+    const size_t n = (size_t)X * Y;
+    const size_t chunk = (size_t)kDC * n * 4;
+    const size_t nblk = (n + kDiffNT - 1) / kDiffNT;
+    const size_t nchunks = (D + kDC - 1) / kDC;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off += (bytes + 255) & ~(size_t)255; };
+    take(n * 4); take(n * 4);                              // float grey
+    take(n); take(n);                                      // integer grey of the uint8 images
+    take(n * 4); take(n * 4); take(n * 4); take(n * 4);    // pixel and arm words
+    take((size_t)X * (Y + wy) * 4); take((size_t)X * (Y + wy) * 4);
+    take(n * 4); take(n * 4);                              // keys (written by the support pass)
+    take(n * 4); take(n * 4 * 3); take(n * 4); take(n * 4); // support size, softmax state, accumulators
+    take(chunk); take(chunk); take(chunk); take(chunk);   // slabs
+    take((size_t)B * nchunks * nblk * 16);                 // parameter-gradient partials
+    return off;
+}
+
+cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
+{
+    const int X = a.W, Y = a.H, n = X * Y;
+    const size_t chunk = (size_t)kDC * n;
+    char *w = (char *)a.ws;
+    auto take = [&](size_t bytes) {
+        char *p = w;
+        w += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    float *gl = (float *)take(n * 4), *gr = (float *)take(n * 4);
+    uint8_t *ql = (uint8_t *)take(n), *qr = (uint8_t *)take(n);
+    uint32_t *pixl = (uint32_t *)take(n * 4), *pixr = (uint32_t *)take(n * 4);
+    uint32_t *arml = (uint32_t *)take(n * 4), *armr = (uint32_t *)take(n * 4);
+    uint32_t *armcl = (uint32_t *)take((size_t)X * (Y + a.wy) * 4);
+    uint32_t *armcr = (uint32_t *)take((size_t)X * (Y + a.wy) * 4);
+    uint32_t *keyl = (uint32_t *)take(n * 4), *keyr = (uint32_t *)take(n * 4);
+    float *ns = (float *)take(n * 4), *state = (float *)take(n * 4 * 3);
+    float *accl = (float *)take(n * 4), *accr = (float *)take(n * 4);
+    float *s0 = (float *)take(chunk * 4), *s1 = (float *)take(chunk * 4), *s2 = (float *)take(chunk * 4);
+    float *s3 = (float *)take(chunk * 4);
+    float *part = (float *)w;
+    const int nblk = (n + kDiffNT - 1) / kDiffNT;
+    const int nchunks = (a.D + kDC - 1) / kDC;
+    const float inv_tau = 1.f / a.tau;
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < a.B; ++b) {
+        const float *L = a.left + (size_t)b * n * 3, *R = a.right + (size_t)b * n * 3;
+        diff_grey_kernel<<<dim3(nblk, 2), kDiffNT, 0, s>>>(L, R, gl, gr, n);
+        if ((e = launch_grey(a.left_u8 + (size_t)b * n * 3, a.right_u8 + (size_t)b * n * 3, ql, qr, X, Y, s)) !=
+                cudaSuccess ||
+            (e = launch_support(ql, qr, pixl, pixr, arml, armr, armcl, armcr, keyl, keyr, a.err, X, Y, a.wx, a.wy,
+                                a.tc, s)) != cudaSuccess)
+            return e;
+        diff_nsupport_kernel<<<nblk, kDiffNT, 0, s>>>(arml, X, Y, ns);
+        if (a.backward) {
+            if ((e = cudaMemsetAsync(accl, 0, (size_t)n * 4, s)) != cudaSuccess ||
+                (e = cudaMemsetAsync(accr, 0, (size_t)n * 4, s)) != cudaSuccess)
+                return e;
+        }
+        float *dh = a.dhat + (size_t)b * n, *st = a.stats + (size_t)b * n * 2;
+        for (int c = 0; c < nchunks; ++c) {
+            const int d0 = c * kDC, dc = min(kDC, a.D - d0);
+            diff_costx_kernel<<<Y, kDiffNT, (size_t)X * 4, s>>>(gl, gr, pixl, pixr, arml, a.theta, X, Y, a.D, d0,
+                                                                dc, s0);
+            if (!a.backward) {
+                diff_vagg_softmax_kernel<<<nblk, kDiffNT, 0, s>>>(s0, arml, ns, X, Y, a.D, d0, dc, inv_tau, state,
+                                                                  c == 0, c == nchunks - 1, dh, st);
+            } else {
+                diff_gca_kernel<<<nblk, kDiffNT, 0, s>>>(s0, arml, ns, X, Y, a.D, d0, dc, inv_tau, dh, st,
+                                                         a.grad_dhat + (size_t)b * n, s1);
+                diff_vT_kernel<<<nblk, kDiffNT, 0, s>>>(s1, arml, X, Y, a.wy, dc, s2);
+                diff_hT_kernel<<<nblk, kDiffNT, 0, s>>>(s2, arml, X, Y, a.wx, dc, s3);
+                diff_costgrad_kernel<<<nblk, kDiffNT, 0, s>>>(gl, gr, pixl, pixr, a.theta, X, Y, a.D, d0, dc, s3,
+                                                              accl, accr,
+                                                              part + ((size_t)b * nchunks + c) * nblk * 4);
+            }
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if (a.backward)
+            diff_finish_kernel<<<nblk, kDiffNT, 0, s>>>(accl, accr, n, a.grad_left + (size_t)b * n * 3,
+                                                        a.grad_right + (size_t)b * n * 3);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (a.backward) {
+        diff_theta_reduce_kernel<<<1, 32, 0, s>>>(part, a.B * nchunks * nblk, a.grad_theta);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace stereo

@@ -55,6 +55,26 @@ struct BatchArgs {
 // Launches the persistent batch kernel with tile shape `tile` on nsm CTAs.
 cudaError_t launch_costagg_batch(BatchArgs &b, int tile, int nsm, cudaStream_t s);
 
+// Differentiable form (diff.cu): B pairs of W x H at processed resolution.
+struct DiffArgs {
+    int B, W, H, D;
+    const float *left, *right;         // [B][H][W][3] float RGB on [0, 1]
+    const uint8_t *left_u8, *right_u8; // [B][H][W][3] uint8 RGB the frozen supports come from
+    const float *theta;                // [4] w_AD, w_MC, lambda_AD, lambda_MC
+    float tau;
+    float *dhat;                       // [B][H][W]
+    float *stats;                      // [B][H][W][2] softmax max and sum (written by forward)
+    const float *grad_dhat;            // backward only
+    float *grad_left, *grad_right;     // backward only, [B][H][W][3]
+    float *grad_theta;                 // backward only, [4]
+    int backward;
+    void *ws;                          // diff_workspace_bytes(W, H, wy, B, D) bytes
+    uint32_t *err;
+    int wx, wy, tc;
+};
+size_t diff_workspace_bytes(int X, int Y, int wy, int B, int D);
+cudaError_t diff_run(const DiffArgs &a, cudaStream_t s);
+
 // Launchers (each returns the launch error, cudaSuccess on success).
 cudaError_t launch_grey(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t *g_l, uint8_t *g_r,
                         int W, int H, cudaStream_t s);

@@ -79,6 +79,8 @@ struct stereo_ctx {
     std::map<int, cudaGraphExec_t> bexec;   // one graph per batch size, updated in place
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
     std::map<std::string, int> tune;
+    void *dws = nullptr;            // workspace of the differentiable form
+    size_t dws_size = 0;
     int last_batch_tile = -1;
     float last_batch_tune_ms[kNumTiles] = {};
 };
@@ -408,6 +410,7 @@ void stereo_destroy(stereo_ctx *c)
                 if (ev) cudaEventDestroy(ev);
         if (c->ws) cudaFree(c->ws);
         if (c->bws) cudaFree(c->bws);
+        if (c->dws) cudaFree(c->dws);
         for (auto &kv : c->bexec) cudaGraphExecDestroy(kv.second);
         for (cudaEvent_t ev : {c->ev_in, c->ev_out, c->ev_t0, c->ev_t1})
             if (ev) cudaEventDestroy(ev);
@@ -907,6 +910,99 @@ int stereo_tune_load(stereo_ctx *c, const char *path)
     }
     fclose(f);
     return n;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- differentiable form
+
+namespace {
+
+int diff_common(stereo_ctx *c, int B, int W, int H, int D, const float *l, const float *r, const uint8_t *lu,
+                const uint8_t *ru, const float *theta, float tau, DiffArgs &a)
+{
+    if (!l || !r || !lu || !ru || !theta) return fail(c, STEREO_EINVAL, "NULL input");
+    if (B < 1 || B > 64 || W < 1 || H < 1 || W > 4096 || H > 8192 || D < 1 || D > 256 || !(tau > 0.f))
+        return fail(c, STEREO_EINVAL, "bad B, W, H, D or tau");
+    const size_t need = diff_workspace_bytes(W, H, c->p.wy, B, D);
+    if (need > c->dws_size) {
+        if (c->mem_cap && need + c->ws_size + c->bws_size > c->mem_cap)
+            return fail(c, STEREO_ENOMEM, "differentiable workspace of %zu bytes exceeds the cap", need);
+        if (c->dws) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->dws);
+            c->dws = nullptr;
+            c->dws_size = 0;
+        }
+        if (cudaMalloc(&c->dws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, STEREO_ENOMEM, "cudaMalloc(%zu) failed", need);
+        }
+        c->dws_size = need;
+    }
+    a = DiffArgs{};
+    a.B = B;
+    a.W = W;
+    a.H = H;
+    a.D = D;
+    a.left = l;
+    a.right = r;
+    a.left_u8 = lu;
+    a.right_u8 = ru;
+    a.theta = theta;
+    a.tau = tau;
+    a.ws = c->dws;
+    a.err = c->d_err;
+    a.wx = c->p.wx;
+    a.wy = c->p.wy;
+    a.tc = c->p.tc;
+    return STEREO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stereo_diff_forward(stereo_ctx *c, int B, int W, int H, int D, const float *left, const float *right,
+                        const uint8_t *left_u8, const uint8_t *right_u8, const float *theta, float tau,
+                        float *dhat, float *stats, void *stream)
+{
+    if (!c) return STEREO_EINVAL;
+    c->err.clear();
+    if (!dhat || !stats) return fail(c, STEREO_EINVAL, "NULL output");
+    DeviceGuard g(c->device);
+    DiffArgs a;
+    int rc = diff_common(c, B, W, H, D, left, right, left_u8, right_u8, theta, tau, a);
+    if (rc != STEREO_OK) return rc;
+    a.dhat = dhat;
+    a.stats = stats;
+    a.backward = 0;
+    cudaError_t e = diff_run(a, stream ? (cudaStream_t)stream : c->stream);
+    return e == cudaSuccess ? STEREO_OK : cuda_fail(c, e, "kernel launch");
+}
+
+int stereo_diff_backward(stereo_ctx *c, int B, int W, int H, int D, const float *left, const float *right,
+                         const uint8_t *left_u8, const uint8_t *right_u8, const float *theta, float tau,
+                         const float *dhat, const float *stats, const float *grad_dhat, float *grad_left,
+                         float *grad_right, float *grad_theta, void *stream)
+{
+    if (!c) return STEREO_EINVAL;
+    c->err.clear();
+    if (!dhat || !stats || !grad_dhat || !grad_left || !grad_right || !grad_theta)
+        return fail(c, STEREO_EINVAL, "NULL argument");
+    DeviceGuard g(c->device);
+    DiffArgs a;
+    int rc = diff_common(c, B, W, H, D, left, right, left_u8, right_u8, theta, tau, a);
+    if (rc != STEREO_OK) return rc;
+    a.dhat = const_cast<float *>(dhat);
+    a.stats = const_cast<float *>(stats);
+    a.grad_dhat = grad_dhat;
+    a.grad_left = grad_left;
+    a.grad_right = grad_right;
+    a.grad_theta = grad_theta;
+    a.backward = 1;
+    cudaError_t e = diff_run(a, stream ? (cudaStream_t)stream : c->stream);
+    return e == cudaSuccess ? STEREO_OK : cuda_fail(c, e, "kernel launch");
 }
 
 }  // extern "C"

@@ -1,0 +1,143 @@
+"""Differentiable form on the GPU (FP32) against the FP64 oracle.
+
+Tolerances come from FP32 rounding: each aggregated cost is a direct sum of
+at most (2 wx + 1) + (2 wy + 1) rounded terms, so its relative error is about
+1e-5 at most (expf adds a few ulp per term); the softmax argument
+z = -CA / tau then moves by at most |z| 1e-5, and dhat by at most
+sum_d p_d |d - dhat| max |dz| <= D max|z| 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_00488_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_00488_gb300 import build
+    build.build()
+
+
+THETA = [1.0, 1.0, 0.3, 2.3]
+
+
+def _inputs(W, H, D, B=1, seed=0):
+    u8l, u8r, gts = [], [], []
+    for b in range(B):
+        s = scenes.make_scene(W, H, D, planes=6, seed=seed + b)
+        u8l.append(s.left)
+        u8r.append(s.right)
+        gts.append(s.disp)
+    u8l, u8r = np.stack(u8l), np.stack(u8r)
+    fl = (u8l.astype(np.float32) / 255.0)
+    fr = (u8r.astype(np.float32) / 255.0)
+    return u8l, u8r, fl, fr, np.stack(gts)
+
+
+def _oracle(u8l, u8r, fl, fr, D, theta, tau, go=None, wx=21, wy=31, tc=13):
+    ql, qr = oracle.grey(u8l), oracle.grey(u8r)
+    gl, gr = oracle.grey_f(fl.astype(np.float64)), oracle.grey_f(fr.astype(np.float64))
+    args = (gl, gr, oracle.census(ql), oracle.census(qr), oracle.arms(ql, wx, wy, tc), D, np.array(theta, np.float64))
+    return oracle.diff_forward_backward(*args, tau=tau, go=go)
+
+
+def _gpu(u8l, u8r, fl, fr, D, theta, tau, go=None, st=None):
+    from paper_2212_00488_gb300 import Stereo
+    from paper_2212_00488_gb300.diff import soft_argmin_disparity
+    st = st or Stereo(0, downscale=0)
+    L = torch.from_numpy(fl).cuda().requires_grad_(go is not None)
+    R = torch.from_numpy(fr).cuda().requires_grad_(go is not None)
+    T = torch.tensor(theta, dtype=torch.float32, device="cuda", requires_grad=go is not None)
+    dh = soft_argmin_disparity(L, R, T, torch.from_numpy(u8l).cuda(), torch.from_numpy(u8r).cuda(), D, tau, st)
+    if go is None:
+        return dh.detach().cpu().numpy().astype(np.float64)
+    (dh * torch.from_numpy(go.astype(np.float32)).cuda()).sum().backward()
+    torch.cuda.synchronize()
+    return (dh.detach().cpu().numpy().astype(np.float64), L.grad.cpu().numpy().astype(np.float64),
+            R.grad.cpu().numpy().astype(np.float64), T.grad.cpu().numpy().astype(np.float64))
+
+
+def _grey_grad(g_rgb):
+    w = np.array([77.0, 150.0, 29.0]) / 256.0
+    # the oracle returns d/d grey; the GPU returns d/d rgb = d/d grey * w
+    return g_rgb[..., 0] / w[0]
+
+
+def test_forward_matches_fp64_within_the_rounding_bound():
+    D, tau = 16, 0.1
+    u8l, u8r, fl, fr, _ = _inputs(96, 64, D, seed=3)
+    g = _gpu(u8l, u8r, fl, fr, D, THETA, tau)[0]
+    o = _oracle(u8l[0], u8r[0], fl[0], fr[0], D, THETA, tau)
+    zmax = 2.0 / tau                  # normalised costs are below w_AD + w_MC
+    bound = D * zmax * 1e-5
+    err = np.abs(g - o)
+    assert err.max() <= bound, (err.max(), bound)
+    assert err.mean() <= bound / 50
+
+
+def test_backward_matches_fp64_gradient():
+    D, tau = 12, 0.1
+    u8l, u8r, fl, fr, _ = _inputs(80, 56, D, seed=5)
+    go = np.random.default_rng(1).normal(size=(1, 56, 80))
+    dh, gl, gr, gt = _gpu(u8l, u8r, fl, fr, D, THETA, tau, go=go)
+    odh, ogl, ogr, ogt = _oracle(u8l[0], u8r[0], fl[0], fr[0], D, THETA, tau, go=go[0])
+    for got, want in ((_grey_grad(gl[0]), ogl), (_grey_grad(gr[0]), ogr)):
+        assert np.linalg.norm(got - want) <= 2e-3 * np.linalg.norm(want)
+        assert np.abs(got - want).max() <= 2e-3 * np.abs(want).max()
+    # the rgb channels are the grey gradient times the grey weights
+    w = np.array([77.0, 150.0, 29.0]) / 256.0
+    assert np.allclose(gl[0], _grey_grad(gl[0])[..., None] * w, rtol=1e-6, atol=1e-12)
+    assert np.allclose(gt, ogt, rtol=2e-3, atol=1e-4 * np.abs(ogt).max())
+
+
+def test_autograd_l1_loss_against_finite_differences_and_determinism():
+    from paper_2212_00488_gb300 import Stereo
+    from paper_2212_00488_gb300.diff import soft_argmin_disparity
+    D, tau = 12, 0.1
+    u8l, u8r, fl, fr, gt = _inputs(72, 48, D, B=2, seed=7)
+    st = Stereo(0, downscale=0)
+    L, R = torch.from_numpy(fl).cuda(), torch.from_numpy(fr).cuda()
+    UL, UR = torch.from_numpy(u8l).cuda(), torch.from_numpy(u8r).cuda()
+    GT = torch.from_numpy(gt.astype(np.float32)).cuda()
+
+    def loss_of(theta, grad=False):
+        T = torch.tensor(theta, dtype=torch.float64).float().cuda().requires_grad_(grad)
+        dh = soft_argmin_disparity(L, R, T, UL, UR, D, tau, st)
+        loss = (dh - GT).abs().mean()
+        if grad:
+            loss.backward()
+            return loss.item(), T.grad.double().cpu().numpy()
+        return loss.item()
+
+    base, g1 = loss_of(THETA, grad=True)
+    _, g2 = loss_of(THETA, grad=True)
+    assert np.array_equal(g1, g2)                     # deterministic backward
+    h = 1e-3
+    for k in range(4):
+        tp, tm = list(THETA), list(THETA)
+        tp[k] += h
+        tm[k] -= h
+        fd = (loss_of(tp) - loss_of(tm)) / (2 * h)
+        # FP32 loss of order 1: the central difference carries about 1e-4 of noise
+        assert abs(fd - g1[k]) <= 2e-3 + 2e-2 * abs(g1[k]), (k, fd, g1[k])
+
+
+def test_paper_shape_batch_of_four():
+    # 4 pairs of 718 x 496 with 73 disparities; pair 0 against the FP64 oracle
+    D, tau = 73, 0.1
+    u8l, u8r, fl, fr, _ = _inputs(718, 496, D, B=4, seed=11)
+    go = np.random.default_rng(2).normal(size=(4, 496, 718))
+    dh, gl, gr, gt = _gpu(u8l, u8r, fl, fr, D, THETA, tau, go=go)
+    odh, ogl, ogr, ogt = _oracle(u8l[0], u8r[0], fl[0], fr[0], D, THETA, tau, go=go[0])
+    bound = D * (2.0 / tau) * 1e-5
+    assert np.abs(dh[0] - odh).max() <= bound
+    assert np.linalg.norm(_grey_grad(gl[0]) - ogl) <= 2e-3 * np.linalg.norm(ogl)
+    assert np.linalg.norm(_grey_grad(gr[0]) - ogr) <= 2e-3 * np.linalg.norm(ogr)
+    assert np.all(np.isfinite(gt))
