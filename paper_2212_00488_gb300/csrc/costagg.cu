@@ -191,17 +191,21 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             for (int q = 0; q < T::DS; ++q)
                 if (xb + k >= d0 + q && xb + k < X) inimg |= 1u << (k * T::DS + q);
         const bool all_in = __all_sync(0xffffffffu, inimg == (1u << (T::KE * T::DS)) - 1u);
-        for (int y = pw; y < Y; y += T::NPW) {
-            const int s = y % T::RS;
-            // loads first: they overlap the wait for the slot
+        // Two register sets of pixels: the warp's next row is loaded while
+        // the current one is turned into prefix rows.
+        uint32_t pv0[T::KE], qv0[T::KE + T::DS - 1];
+        auto load = [&](int y, uint32_t (&pv)[T::KE], uint32_t (&qv)[T::KE + T::DS - 1]) {
+            if (y >= Y) return;
             const uint32_t *pl = a.pix_l + (size_t)y * X;
             const uint32_t *pr = a.pix_r + (size_t)y * X;
-            uint32_t pv[T::KE], qv[T::KE + T::DS - 1];
 #pragma unroll
             for (int k = 0; k < T::KE; ++k) pv[k] = __ldg(pl + offl[k]);
 #pragma unroll
             for (int k = 0; k < T::KE + T::DS - 1; ++k) qv[k] = __ldg(pr + offr[k]);
-            if (y >= T::RS && !mbar_wait_warp(&empty[s], ((y / T::RS) - 1) & 1, limit, a.err)) return;
+        };
+        auto produce = [&](int y, const uint32_t (&pv)[T::KE], const uint32_t (&qv)[T::KE + T::DS - 1]) -> bool {
+            const int s = y % T::RS;
+            if (y >= T::RS && !mbar_wait_warp(&empty[s], ((y / T::RS) - 1) & 1, limit, a.err)) return false;
             uint32_t c[T::DS][T::KE];
             uint32_t run[T::DS];
 #pragma unroll
@@ -235,6 +239,11 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 if (lane == 0) row[0] = 0;
             }
             mbar_arrive(&full[s]);
+            return true;
+        };
+        for (int y = pw; y < Y; y += T::NPW) {
+            load(y, pv0, qv0);
+            if (!produce(y, pv0, qv0)) return;
         }
         return;
     }
@@ -260,7 +269,6 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     const SType *srow0 = sx + (g * T::DPT) * T::SWP + x + wx + (b ? g * T::DPT : 0);
     const int rows = Y + wy;                      // row steps: inputs 0..Y-1, outputs lag by wy
 
-    uint32_t am0 = __ldg(armc), am1 = __ldg(armc + (size_t)min(1, rows - 1) * X), am2;
     {
         Vec z;
 #pragma unroll
@@ -270,50 +278,77 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     uint32_t V[T::DPT];
 #pragma unroll
     for (int k = 0; k < T::DPT; ++k) V[k] = 0;
-    auto step = [&](int y, uint32_t am) -> bool {
-        const int s = y % T::RS;
-        if (y < Y) {
-            if (!mbar_wait_warp(&full[s], (y / T::RS) & 1, limit, a.err)) return false;
-            const SType *r0 = srow0 + s * (T::DS * T::SWP);
-            const int hi = ((am >> 8) & 0xFF) + 1, lo = am & 0xFF;
-            Vec w;
+
+    // x-window sums of one input row for this thread's disparities
+    auto hsum = [&](int y, uint32_t am, uint32_t (&cax)[T::DPT]) {
+        const SType *r0 = srow0 + (y % T::RS) * (T::DS * T::SWP);
+        const int hi = ((am >> 8) & 0xFF) + 1, lo = am & 0xFF;
 #pragma unroll
-            for (int k = 0; k < T::DPT; ++k) {
-                const SType *rk = r0 + k * (T::SWP + (b ? 1 : 0));
-                uint32_t cax = (uint32_t)rk[hi] - (uint32_t)rk[-lo];
-                if (T::S16) cax &= 0xFFFFu;
-                V[k] += cax;
-                vget<T::DPT>(w, k) = V[k];
-            }
-            myring[((y + 1) & (kRing - 1)) * T::NCT] = w;
-            mbar_arrive(&empty[s]);
+        for (int k = 0; k < T::DPT; ++k) {
+            const SType *rk = r0 + k * (T::SWP + (b ? 1 : 0));
+            uint32_t c = (uint32_t)rk[hi] - (uint32_t)rk[-lo];
+            if (T::S16) c &= 0xFFFFu;
+            cax[k] = c;
         }
-        const int yo = y - wy;
-        if (yo >= 0) {
-            const int up = (am >> 16) & 0xFF, down = am >> 24;
-            Vec vh = myring[((yo + down + 1) & (kRing - 1)) * T::NCT];
-            Vec vl = myring[((yo - up) & (kRing - 1)) * T::NCT];
-            uint32_t best = 0xFFFFFFFFu;
-#pragma unroll
-            for (int k = 0; k < T::DPT; ++k) {
-                const uint32_t kk = ((vget<T::DPT>(vh, k) - vget<T::DPT>(vl, k)) << 8) | (uint32_t)(dg + k);
-                best = (dg + k < D) ? min(best, kk) : best;
-            }
-#pragma unroll
-            for (int o = 1; o < T::G; o <<= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-            if (g == 0 && valid) atomicMin(key + (size_t)yo * X, best);
-        }
-        return true;
     };
-    for (int y = 0; y < rows; y += 3) {
-        am2 = __ldg(armc + (size_t)min(y + 2, rows - 1) * X);
-        if (!step(y, am0)) return;
-        if (y + 1 >= rows) break;
-        am0 = __ldg(armc + (size_t)min(y + 3, rows - 1) * X);
-        if (!step(y + 1, am1)) return;
-        if (y + 2 >= rows) break;
-        am1 = __ldg(armc + (size_t)min(y + 4, rows - 1) * X);
-        if (!step(y + 2, am2)) return;
+    auto push = [&](int y, const uint32_t (&cax)[T::DPT]) {
+        Vec w;
+#pragma unroll
+        for (int k = 0; k < T::DPT; ++k) {
+            V[k] += cax[k];
+            vget<T::DPT>(w, k) = V[k];
+        }
+        myring[((y + 1) & (kRing - 1)) * T::NCT] = w;
+    };
+    // packed WTA key of output row yo over this thread's disparities
+    auto vkey = [&](int yo, uint32_t am) -> uint32_t {
+        const int up = (am >> 16) & 0xFF, down = am >> 24;
+        Vec vh = myring[((yo + down + 1) & (kRing - 1)) * T::NCT];
+        Vec vl = myring[((yo - up) & (kRing - 1)) * T::NCT];
+        uint32_t best = 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < T::DPT; ++k) {
+            const uint32_t kk = ((vget<T::DPT>(vh, k) - vget<T::DPT>(vl, k)) << 8) | (uint32_t)(dg + k);
+            best = (dg + k < D) ? min(best, kk) : best;
+        }
+        return best;
+    };
+
+    // Two rows per step, so that the loads of both rows are in flight
+    // together. Arm words are fetched two steps ahead.
+    uint32_t a0 = __ldg(armc), a1 = __ldg(armc + (size_t)min(1, rows - 1) * X);
+    for (int y = 0; y < rows; y += 2) {
+        const uint32_t n0 = __ldg(armc + (size_t)min(y + 2, rows - 1) * X);
+        const uint32_t n1 = __ldg(armc + (size_t)min(y + 3, rows - 1) * X);
+        const bool two = y + 1 < rows;
+        const bool in0 = y < Y, in1 = two && y + 1 < Y;
+        if (in0 && !mbar_wait_warp(&full[y % T::RS], (y / T::RS) & 1, limit, a.err)) return;
+        if (in1 && !mbar_wait_warp(&full[(y + 1) % T::RS], ((y + 1) / T::RS) & 1, limit, a.err)) return;
+        uint32_t c0[T::DPT], c1[T::DPT];
+        if (in0) hsum(y, a0, c0);
+        if (in1) hsum(y + 1, a1, c1);
+        if (in0) mbar_arrive(&empty[y % T::RS]);
+        if (in1) mbar_arrive(&empty[(y + 1) % T::RS]);
+        // Row yo0 reads V down to slot y - 2wy, which shares its ring slot
+        // with y + 2 when wy = 31, so its key is taken before row y + 1 is
+        // pushed.
+        const int yo0 = y - wy, yo1 = y + 1 - wy;
+        const bool out0 = yo0 >= 0, out1 = two && yo1 >= 0;
+        if (in0) push(y, c0);
+        uint32_t k0 = out0 ? vkey(yo0, a0) : 0u;
+        if (in1) push(y + 1, c1);
+        uint32_t k1 = out1 ? vkey(yo1, a1) : 0u;
+#pragma unroll
+        for (int o = 1; o < T::G; o <<= 1) {
+            k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, o));
+            k1 = min(k1, __shfl_xor_sync(0xffffffffu, k1, o));
+        }
+        if (g == 0 && valid) {
+            if (out0) atomicMin(key + (size_t)yo0 * X, k0);
+            if (out1) atomicMin(key + (size_t)yo1 * X, k1);
+        }
+        a0 = n0;
+        a1 = n1;
     }
 }
 

@@ -94,6 +94,26 @@ def test_every_tile_shape(tile):
     _compare(_run_gpu(s.left, s.right, 50, p, tile=tile), oracle.pipeline(s.left, s.right, 50, p), f"tile {tile}")
 
 
+def _flat_blocks(W, H, shift, seed):
+    # large flat blocks with faint noise: support arms run to their caps, so
+    # vertical windows span the full 2 wy + 1 rows of the ring
+    rng = np.random.default_rng(seed)
+    base = np.kron(rng.integers(40, 220, size=(H // 64 + 1, W // 48 + 2)), np.ones((64, 48)))
+    img = np.clip(base[:H, :W + shift] + rng.integers(-2, 3, size=(H, W + shift)), 0, 255).astype(np.uint8)
+    left = np.repeat(img[:, shift:, None], 3, axis=2)
+    right = np.repeat(img[:, :W, None], 3, axis=2)
+    return np.ascontiguousarray(left), np.ascontiguousarray(right)
+
+
+@pytest.mark.parametrize("tile", range(6))
+def test_full_vertical_arms_every_tile(tile):
+    left, right = _flat_blocks(170, 200, 7, seed=tile)
+    p = _params(downscale=0)
+    r = oracle.pipeline(left, right, 24, p)
+    assert max(int(r.arms_l[2].max()), int(r.arms_l[3].max())) == p.wy     # arms reach the cap
+    _compare(_run_gpu(left, right, 24, p, tile=tile), r, f"flat tile {tile}")
+
+
 @pytest.mark.parametrize("W,H,dmax,ds", [
     (7, 5, 3, 0),        # narrower than a warp, fewer rows than the vertical arm cap
     (1, 9, 1, 0),        # one column, one disparity
