@@ -101,14 +101,15 @@ struct Tile {
     using SType = typename std::conditional<S16_, uint16_t, uint32_t>::type;
     static constexpr int G = DS / DPT;        // consumer threads per column (adjacent lanes)
     static constexpr int LPX = 32 / G;        // columns per consumer warp
-    static constexpr int NCT = 2 * XS * G;    // consumer threads
+    static constexpr int NCT = 2 * XS * G;    // consumer threads with a column
+    static constexpr int NCTP = (NCT + 31) / 32 * 32;   // consumer threads, whole warps
     static constexpr int NPW = NPW_;          // producer warps; warp p fills rows y = p (mod NPW)
     static constexpr int NP = 32 * NPW;
-    static constexpr int NT = NCT + NP;
+    static constexpr int NT = NCTP + NP;
     static constexpr int NE = 32 * KE;        // S[0..NE]
     // S row pitch in elements: the G groups of a consumer warp read rows that
-    // start LPX words apart modulo the 32 banks
-    static constexpr int SWP = NE + (S16 ? 2 * LPX : LPX);
+    // start LPX words apart modulo the 32 banks (with one group any pitch does)
+    static constexpr int SWP = NE + (G == 1 ? 4 : S16 ? 2 * LPX : LPX);
     static constexpr int B_BAR = 2 * RS * 8;
     static constexpr int B_RING = kRing * NCT * DPT * 4;
     static constexpr int B_SX = RS * DS * SWP * (int)sizeof(SType);
@@ -117,7 +118,7 @@ struct Tile {
     static_assert(DS % DPT == 0 && 32 % G == 0, "the threads of a column sit in adjacent lanes of one warp");
     static_assert(DPT == 2 || DPT == 4, "ring entries are 8 or 16 bytes");
     static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
-    static_assert(NCT % 32 == 0 && NT <= 1024, "");
+    static_assert(NT <= 1024, "");
     static_assert(RS >= NPW, "every producer warp needs a slot of its own");
     static_assert(BYTES <= 232448, "tile exceeds shared memory");
 };
@@ -167,14 +168,14 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 mbar_inval(&empty[s]);
             }
             mbar_init(&full[s], 32);                // the producing warp
-            mbar_init(&empty[s], T::NCT);           // every consumer
+            mbar_init(&empty[s], T::NCTP);          // every consumer thread
         }
     }
     __syncthreads();
 
-    if (t >= T::NCT) {
+    if (t >= T::NCTP) {
         // ======================= producers: warp pw fills rows pw, pw+4, ...
-        const int pw = (t - T::NCT) >> 5;
+        const int pw = (t - T::NCTP) >> 5;
         const uint32_t P = a.P;
         const int xb = x0 - wx + lane * T::KE;      // x of this lane's first entry
         // per-lane constants: clamped load offsets and, per (entry, disparity),
@@ -191,8 +192,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             for (int q = 0; q < T::DS; ++q)
                 if (xb + k >= d0 + q && xb + k < X) inimg |= 1u << (k * T::DS + q);
         const bool all_in = __all_sync(0xffffffffu, inimg == (1u << (T::KE * T::DS)) - 1u);
-        // Two register sets of pixels: the warp's next row is loaded while
-        // the current one is turned into prefix rows.
+        // pixels of one row: the lane's KE entries and their KE + DS - 1 matches
         uint32_t pv0[T::KE], qv0[T::KE + T::DS - 1];
         auto load = [&](int y, uint32_t (&pv)[T::KE], uint32_t (&qv)[T::KE + T::DS - 1]) {
             if (y >= Y) return;
@@ -254,22 +254,26 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     // warps since G divides 32)
     const int g = t & (T::G - 1);                 // disparity group of this thread
     const int ci = t / T::G;
+    // threads past the last column only keep the hand-off going
+    const bool active = T::NCT == T::NCTP || t < T::NCT;
     const int b = ci >= T::XS;
-    const int x = ci - b * T::XS;
+    const int x = active ? ci - b * T::XS : T::XS - 1;
     const int col = b ? x0 - d0 + x : x0 + x;
-    const bool valid = col >= 0 && col < X;
+    const bool valid = active && col >= 0 && col < X;
     const int colc = min(max(col, 0), X - 1);
     const int dg = d0 + g * T::DPT;               // first disparity of the group
     uint32_t *key = (b ? a.key_r : a.key_l) + colc;
     // combined arm words: row r holds the left/right arms of row r (low half)
     // and the up/down arms of row r - wy (high half)
     const uint32_t *armc = (b ? a.armc_r : a.armc_l) + colc;
-    Vec *myring = ring + t;
+    // ring entries of this thread (an idle thread reads the last column's
+    // entries and never writes)
+    Vec *myring = ring + (active ? t : T::NCT - 1);
     // S element of this pixel's own column for the group's first disparity
     const SType *srow0 = sx + (g * T::DPT) * T::SWP + x + wx + (b ? g * T::DPT : 0);
     const int rows = Y + wy;                      // row steps: inputs 0..Y-1, outputs lag by wy
 
-    {
+    if (active) {
         Vec z;
 #pragma unroll
         for (int k = 0; k < T::DPT; ++k) vget<T::DPT>(z, k) = 0;
@@ -298,7 +302,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             V[k] += cax[k];
             vget<T::DPT>(w, k) = V[k];
         }
-        myring[((y + 1) & (kRing - 1)) * T::NCT] = w;
+        if (active) myring[((y + 1) & (kRing - 1)) * T::NCT] = w;
     };
     // packed WTA key of output row yo over this thread's disparities
     auto vkey = [&](int yo, uint32_t am) -> uint32_t {
@@ -314,49 +318,93 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         return best;
     };
 
-    // Two rows per step, so that the loads of both rows are in flight
-    // together. Arm words are fetched two steps ahead.
+    // Two rows per step. While both rows are inputs the step has no branch
+    // but the waits, so the loads and arithmetic of the two rows interleave;
+    // idle threads and rows without an output do the same work and drop it.
+    // Arm words are fetched a step ahead.
     uint32_t a0 = __ldg(armc), a1 = __ldg(armc + (size_t)min(1, rows - 1) * X);
     for (int y = 0; y < rows; y += 2) {
         const uint32_t n0 = __ldg(armc + (size_t)min(y + 2, rows - 1) * X);
         const uint32_t n1 = __ldg(armc + (size_t)min(y + 3, rows - 1) * X);
-        const bool two = y + 1 < rows;
-        const bool in0 = y < Y, in1 = two && y + 1 < Y;
-        if (in0 && !mbar_wait_warp(&full[y % T::RS], (y / T::RS) & 1, limit, a.err)) return;
-        if (in1 && !mbar_wait_warp(&full[(y + 1) % T::RS], ((y + 1) / T::RS) & 1, limit, a.err)) return;
-        uint32_t c0[T::DPT], c1[T::DPT];
-        if (in0) hsum(y, a0, c0);
-        if (in1) hsum(y + 1, a1, c1);
-        if (in0) mbar_arrive(&empty[y % T::RS]);
-        if (in1) mbar_arrive(&empty[(y + 1) % T::RS]);
-        // Row yo0 reads V down to slot y - 2wy, which shares its ring slot
-        // with y + 2 when wy = 31, so its key is taken before row y + 1 is
-        // pushed.
         const int yo0 = y - wy, yo1 = y + 1 - wy;
-        const bool out0 = yo0 >= 0, out1 = two && yo1 >= 0;
-        if (in0) push(y, c0);
-        uint32_t k0 = out0 ? vkey(yo0, a0) : 0u;
-        if (in1) push(y + 1, c1);
-        uint32_t k1 = out1 ? vkey(yo1, a1) : 0u;
+        uint32_t c0[T::DPT], c1[T::DPT], k0, k1;
+        if (y + 1 < Y) {
+            if (!mbar_wait_warp(&full[y % T::RS], (y / T::RS) & 1, limit, a.err)) return;
+            if (!mbar_wait_warp(&full[(y + 1) % T::RS], ((y + 1) / T::RS) & 1, limit, a.err)) return;
+            hsum(y, a0, c0);
+            hsum(y + 1, a1, c1);
+            mbar_arrive(&empty[y % T::RS]);
+            mbar_arrive(&empty[(y + 1) % T::RS]);
+            // Row yo0 reads V down to slot y - 2wy, which shares its ring
+            // slot with y + 2 when wy = 31, so its key is taken before row
+            // y + 1 is pushed.
+            push(y, c0);
+            k0 = vkey(yo0, a0);
+            push(y + 1, c1);
+            k1 = vkey(yo1, a1);
+        } else {
+            // the last input row (when Y is odd) and the rows that only
+            // output; no V beyond V(Y) is ever read
+            if (y < Y) {
+                if (!mbar_wait_warp(&full[y % T::RS], (y / T::RS) & 1, limit, a.err)) return;
+                hsum(y, a0, c0);
+                mbar_arrive(&empty[y % T::RS]);
+                push(y, c0);
+            }
+            k0 = vkey(yo0, a0);
+            k1 = vkey(yo1, a1);
+        }
 #pragma unroll
         for (int o = 1; o < T::G; o <<= 1) {
             k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, o));
             k1 = min(k1, __shfl_xor_sync(0xffffffffu, k1, o));
         }
         if (g == 0 && valid) {
-            if (out0) atomicMin(key + (size_t)yo0 * X, k0);
-            if (out1) atomicMin(key + (size_t)yo1 * X, k1);
+            if (yo0 >= 0) atomicMin(key + (size_t)yo0 * X, k0);
+            if (yo1 >= 0 && y + 1 < rows) atomicMin(key + (size_t)yo1 * X, k1);
         }
         a0 = n0;
         a1 = n1;
     }
 }
 
+// Tiles of a frame, slab by slab. Slab s (first disparity d0 = s DS) needs
+// strips x0 = 0, XS, ... until both bases are covered: the left base reads
+// columns [x0, x0 + XS), the right base [x0 - d0, x0 - d0 + XS), so
+// ceil((X + d0) / XS) strips; low slabs need fewer than high ones.
+template <class T>
+__host__ __device__ __forceinline__ int slab_strips(const CostAggArgs &a, int slab)
+{
+    return (a.X + slab * T::DS + T::XS - 1) / T::XS;
+}
+
+template <class T>
+__host__ __device__ __forceinline__ int tiles_of(const CostAggArgs &a)
+{
+    int n = 0;
+    for (int s = 0; s * T::DS < a.D; ++s) n += slab_strips<T>(a, s);
+    return n;
+}
+
+template <class T>
+__device__ __forceinline__ void tile_at(const CostAggArgs &a, int tile, int &x0, int &d0)
+{
+    int s = 0;
+    for (int n = slab_strips<T>(a, 0); tile >= n; n = slab_strips<T>(a, s)) {
+        tile -= n;
+        ++s;
+    }
+    x0 = tile * T::XS;
+    d0 = s * T::DS;
+}
+
 template <class T>
 __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    costagg_tile<T>(a, blockIdx.x * T::XS, blockIdx.y * T::DS, smem, false);
+    int x0, d0;
+    tile_at<T>(a, blockIdx.x, x0, d0);
+    costagg_tile<T>(a, x0, d0, smem, false);
 }
 
 // Persistent form for a batch of frames: one CTA per SM takes tiles (job,
@@ -379,9 +427,9 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_batch_kernel(const __grid_co
         if (tile >= b.total_tiles) return;
         int j = 0;
         while (j + 1 < b.njobs && tile >= b.tile_start[j + 1]) ++j;
-        const int local = tile - b.tile_start[j];
-        const int strip = local % b.nstrip[j], slab = local / b.nstrip[j];
-        costagg_tile<T>(b.job[j], strip * T::XS, slab * T::DS, smem, reuse);
+        int x0, d0;
+        tile_at<T>(b.job[j], tile - b.tile_start[j], x0, d0);
+        costagg_tile<T>(b.job[j], x0, d0, smem, reuse);
         reuse = true;
         __syncthreads();
     }
@@ -395,6 +443,7 @@ using T2 = Tile<104, 4, 5, 4, false, 2, 4>;   // wx <= 26, 32-bit prefixes
 using T3 = Tile<96, 4, 7, 4, false, 2, 4>;    // wx <= 29, 32-bit prefixes
 using T4 = Tile<96, 4, 5, 8, true, 4, 4>;     // one consumer thread per column
 using T5 = Tile<64, 4, 5, 8, true, 2, 4>;     // narrow frames
+using T6 = Tile<104, 4, 5, 5, false, 4, 4>;   // wx <= 26, one thread per column and 4 disparities
 
 template <class T>
 bool fits(const CostAggArgs &a)
@@ -404,13 +453,6 @@ bool fits(const CostAggArgs &a)
     return !T::S16 || (uint64_t)(2 * a.wx + 1) * a.P < 65536u;
 }
 
-template <class T>
-void grid_of(const CostAggArgs &a, int &nstrip, int &nslab)
-{
-    nslab = (a.D + T::DS - 1) / T::DS;
-    const int dlast = (nslab - 1) * T::DS;
-    nstrip = (a.X + dlast + T::XS - 1) / T::XS;
-}
 
 template <class T>
 cudaError_t setup_one()
@@ -427,11 +469,8 @@ cudaError_t launch_batch_one(BatchArgs &b, int nsm, cudaStream_t s)
     b.total_tiles = 0;
     for (int j = 0; j < b.njobs; ++j) {
         if (!fits<T>(b.job[j])) return cudaErrorInvalidValue;
-        int nstrip, nslab;
-        grid_of<T>(b.job[j], nstrip, nslab);
-        b.nstrip[j] = nstrip;
         b.tile_start[j] = b.total_tiles;
-        b.total_tiles += nstrip * nslab;
+        b.total_tiles += tiles_of<T>(b.job[j]);
     }
     b.tile_start[b.njobs] = b.total_tiles;
     cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), s);
@@ -445,9 +484,7 @@ cudaError_t launch_batch_one(BatchArgs &b, int nsm, cudaStream_t s)
 template <class T>
 cudaError_t launch_one(const CostAggArgs &a, cudaStream_t s)
 {
-    int nstrip, nslab;
-    grid_of<T>(a, nstrip, nslab);
-    costagg_wta_kernel<T><<<dim3(nstrip, nslab), T::NT, T::BYTES, s>>>(a);
+    costagg_wta_kernel<T><<<tiles_of<T>(a), T::NT, T::BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -455,9 +492,7 @@ template <class T>
 double estimate(const CostAggArgs &a, int nsm)
 {
     // time ~ waves x per-CTA work per row (producer entries + consumer cells)
-    int nstrip, nslab;
-    grid_of<T>(a, nstrip, nslab);
-    const long ctas = (long)nstrip * nslab;
+    const long ctas = tiles_of<T>(a);
     const long waves = (ctas + nsm - 1) / nsm;
     const double work = (double)T::DS * (T::XS + T::DS + 2 * a.wx) + 2.0 * T::XS * T::DS;
     return (double)waves * work * (T::S16 ? 1.0 : 1.05);
@@ -473,7 +508,8 @@ cudaError_t costagg_setup()
     if ((e = setup_one<T2>()) != cudaSuccess) return e;
     if ((e = setup_one<T3>()) != cudaSuccess) return e;
     if ((e = setup_one<T4>()) != cudaSuccess) return e;
-    return setup_one<T5>();
+    if ((e = setup_one<T5>()) != cudaSuccess) return e;
+    return setup_one<T6>();
 }
 
 int costagg_pick(const CostAggArgs &a, int nsm)
@@ -489,6 +525,7 @@ int costagg_pick(const CostAggArgs &a, int nsm)
     consider(3, fits<T3>(a), estimate<T3>(a, nsm) * 1.01);
     consider(4, fits<T4>(a), estimate<T4>(a, nsm));
     consider(5, fits<T5>(a), estimate<T5>(a, nsm) * 1.01);
+    consider(6, fits<T6>(a), estimate<T6>(a, nsm));
     return best;
 }
 
@@ -501,6 +538,7 @@ bool costagg_fits(const CostAggArgs &a, int tile)
     case 3: return fits<T3>(a);
     case 4: return fits<T4>(a);
     case 5: return fits<T5>(a);
+    case 6: return fits<T6>(a);
     default: return false;
     }
 }
@@ -515,6 +553,7 @@ cudaError_t launch_costagg_batch(BatchArgs &b, int tile, int nsm, cudaStream_t s
     case 3: return launch_batch_one<T3>(b, nsm, s);
     case 4: return launch_batch_one<T4>(b, nsm, s);
     case 5: return launch_batch_one<T5>(b, nsm, s);
+    case 6: return launch_batch_one<T6>(b, nsm, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -530,6 +569,7 @@ cudaError_t launch_costagg(const CostAggArgs &a, cudaStream_t s)
     case 3: return fits<T3>(a) ? launch_one<T3>(a, s) : cudaErrorInvalidValue;
     case 4: return fits<T4>(a) ? launch_one<T4>(a, s) : cudaErrorInvalidValue;
     case 5: return fits<T5>(a) ? launch_one<T5>(a, s) : cudaErrorInvalidValue;
+    case 6: return fits<T6>(a) ? launch_one<T6>(a, s) : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

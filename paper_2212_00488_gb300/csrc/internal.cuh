@@ -38,7 +38,7 @@ struct CostAggArgs {
 };
 
 // Number of tile shapes of the fused kernel (ids 0 .. kNumTiles-1).
-constexpr int kNumTiles = 6;
+constexpr int kNumTiles = 7;
 int costagg_pick(const CostAggArgs &a, int nsm);
 bool costagg_fits(const CostAggArgs &a, int tile);
 
@@ -48,7 +48,6 @@ struct BatchArgs {
     int njobs;
     int total_tiles;                  // filled by the launcher
     int tile_start[kMaxBatch + 1];    // first tile of each job (filled by the launcher)
-    int nstrip[kMaxBatch];            // strips per job (filled by the launcher)
     CostAggArgs job[kMaxBatch];       // every job's err points at the same word
     uint32_t *counter;                // tile counter, zeroed by the launcher
 };

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from paper_2212_00488_gb300 import scenes
+from paper_2212_00488_gb300._lib import NUM_TILES
 
 pytestmark = pytest.mark.gpu
 
@@ -85,7 +86,7 @@ def test_paper_shape_full_pipeline():
     _compare(_run_gpu(s.left, s.right, 145, p), oracle.pipeline(s.left, s.right, 145, p), "1436x992/145")
 
 
-@pytest.mark.parametrize("tile", range(6))
+@pytest.mark.parametrize("tile", range(NUM_TILES))
 def test_every_tile_shape(tile):
     # each tile shape of the fused kernel gives the oracle's result, on a frame
     # with ragged strips and slabs and both clipped image borders
@@ -105,7 +106,7 @@ def _flat_blocks(W, H, shift, seed):
     return np.ascontiguousarray(left), np.ascontiguousarray(right)
 
 
-@pytest.mark.parametrize("tile", range(6))
+@pytest.mark.parametrize("tile", range(NUM_TILES))
 def test_full_vertical_arms_every_tile(tile):
     left, right = _flat_blocks(170, 200, 7, seed=tile)
     p = _params(downscale=0)
