@@ -110,7 +110,8 @@ struct Tile {
     // S row pitch in elements: the G groups of a consumer warp read rows that
     // start LPX words apart modulo the 32 banks (with one group any pitch does)
     static constexpr int SWP = NE + (G == 1 ? 4 : S16 ? 2 * LPX : LPX);
-    static constexpr int B_BAR = 2 * RS * 8;
+    static constexpr int NB = RS / 2;         // row pairs (2k, 2k+1) share a full and an empty barrier
+    static constexpr int B_BAR = 2 * NB * 8;
     static constexpr int B_RING = kRing * NCT * DPT * 4;
     static constexpr int B_SX = RS * DS * SWP * (int)sizeof(SType);
     static constexpr int B_LUT = 256 * 8 * 2;
@@ -120,6 +121,7 @@ struct Tile {
     static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
     static_assert(NT <= 1024, "");
     static_assert(RS >= NPW, "every producer warp needs a slot of its own");
+    static_assert(RS % 2 == 0, "slots are handed over in row pairs");
     static_assert(BYTES <= 232448, "tile exceeds shared memory");
 };
 
@@ -149,7 +151,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     using SType = typename T::SType;
     using Vec = typename VecOf<T::DPT>::type;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + T::RS;
+    uint64_t *empty = full + T::NB;
     Vec *ring = reinterpret_cast<Vec *>(smem + T::B_BAR);                     // [64][NCT]
     SType *sx = reinterpret_cast<SType *>(smem + T::B_BAR + T::B_RING);       // [RS][DS][SWP]
     uint16_t *lut = reinterpret_cast<uint16_t *>(smem + T::B_BAR + T::B_RING + T::B_SX);  // [256][8]
@@ -162,12 +164,12 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     if (!reuse)
         for (int i = t; i < 256 * 8; i += T::NT) lut[i] = (uint16_t)(a.lut_ad[i >> 3] + a.lut_mc[i & 7]);
     if (t == 0) {
-        for (int s = 0; s < T::RS; ++s) {
+        for (int s = 0; s < T::NB; ++s) {
             if (reuse) {
                 mbar_inval(&full[s]);
                 mbar_inval(&empty[s]);
             }
-            mbar_init(&full[s], 32);                // the producing warp
+            mbar_init(&full[s], 64);                // the two producing warps of a row pair
             mbar_init(&empty[s], T::NCTP);          // every consumer thread
         }
     }
@@ -203,47 +205,62 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
 #pragma unroll
             for (int k = 0; k < T::KE + T::DS - 1; ++k) qv[k] = __ldg(pr + offr[k]);
         };
-        auto produce = [&](int y, const uint32_t (&pv)[T::KE], const uint32_t (&qv)[T::KE + T::DS - 1]) -> bool {
+        // The next row's pixels are loaded into the same registers as soon
+        // as this row's costs are formed, and the wait for a free slot comes
+        // after the scan, so load latency and hand-off overlap the work.
+        load(pw, pv0, qv0);
+        for (int y = pw; y < Y; y += T::NPW) {
             const int s = y % T::RS;
-            if (y >= T::RS && !mbar_wait_warp(&empty[s], ((y / T::RS) - 1) & 1, limit, a.err)) return false;
             uint32_t c[T::DS][T::KE];
             uint32_t run[T::DS];
+            // the cost loop, with the out-of-image test only in warps that
+            // touch a border
+            auto form = [&](auto border) {
+                constexpr bool kBorder = decltype(border)::value;
 #pragma unroll
-            for (int q = 0; q < T::DS; ++q) run[q] = 0;
+                for (int q = 0; q < T::DS; ++q) run[q] = 0;
 #pragma unroll
-            for (int k = 0; k < T::KE; ++k) {
-                const uint32_t pk = pv[k];
+                for (int k = 0; k < T::KE; ++k) {
+                    const uint32_t pk = pv0[k];
+#pragma unroll
+                    for (int q = 0; q < T::DS; ++q) {
+                        // match of entry k at disparity d0 + q: qv index k + DS-1 - q
+                        const uint32_t qk = qv0[k + T::DS - 1 - q];
+                        const uint32_t ad = (uint32_t)abs((int)(pk & 0xFF) - (int)(qk & 0xFF));
+                        uint32_t v = lut[ad * 8 + __popc((pk ^ qk) & 0x3F00u)];
+                        if (kBorder) v = (inimg >> (k * T::DS + q)) & 1u ? v : P;
+                        run[q] += v;
+                        c[q][k] = run[q];
+                    }
+                }
+            };
+            if (all_in)
+                form(std::false_type{});
+            else
+                form(std::true_type{});
+            load(y + T::NPW, pv0, qv0);
+            uint32_t incl[T::DS];
+#pragma unroll
+            for (int q = 0; q < T::DS; ++q) incl[q] = run[q];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
                 for (int q = 0; q < T::DS; ++q) {
-                    // match of entry k at disparity d0 + q: qv index k + DS-1 - q
-                    const uint32_t qk = qv[k + T::DS - 1 - q];
-                    const uint32_t ad = (uint32_t)abs((int)(pk & 0xFF) - (int)(qk & 0xFF));
-                    uint32_t v = lut[ad * 8 + __popc((pk ^ qk) & 0x3F00u)];
-                    if (!all_in) v = (inimg >> (k * T::DS + q)) & 1u ? v : P;
-                    run[q] += v;
-                    c[q][k] = run[q];
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, incl[q], o);
+                    if (lane >= o) incl[q] += u;
                 }
             }
+            if (y >= T::RS && !mbar_wait_warp(&empty[s >> 1], ((y / T::RS) - 1) & 1, limit, a.err)) return;
 #pragma unroll
             for (int q = 0; q < T::DS; ++q) {
-                uint32_t incl = run[q];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += u;
-                }
-                const uint32_t excl = incl - run[q];
+                const uint32_t excl = incl[q] - run[q];
                 SType *row = sx + (s * T::DS + q) * T::SWP;
 #pragma unroll
                 for (int k = 0; k < T::KE; ++k) row[1 + lane * T::KE + k] = (SType)(excl + c[q][k]);
                 if (lane == 0) row[0] = 0;
             }
-            mbar_arrive(&full[s]);
-            return true;
-        };
-        for (int y = pw; y < Y; y += T::NPW) {
-            load(y, pv0, qv0);
-            if (!produce(y, pv0, qv0)) return;
+            mbar_arrive(&full[s >> 1]);
+            if (y + 1 == Y && (y & 1) == 0) mbar_arrive(&full[s >> 1]);   // a last row without a partner
         }
         return;
     }
@@ -304,68 +321,73 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         }
         if (active) myring[((y + 1) & (kRing - 1)) * T::NCT] = w;
     };
-    // packed WTA key of output row yo over this thread's disparities
-    auto vkey = [&](int yo, uint32_t am) -> uint32_t {
-        const int up = (am >> 16) & 0xFF, down = am >> 24;
-        Vec vh = myring[((yo + down + 1) & (kRing - 1)) * T::NCT];
-        Vec vl = myring[((yo - up) & (kRing - 1)) * T::NCT];
-        uint32_t best = 0xFFFFFFFFu;
-#pragma unroll
-        for (int k = 0; k < T::DPT; ++k) {
-            const uint32_t kk = ((vget<T::DPT>(vh, k) - vget<T::DPT>(vl, k)) << 8) | (uint32_t)(dg + k);
-            best = (dg + k < D) ? min(best, kk) : best;
-        }
-        return best;
-    };
-
     // Two rows per step. While both rows are inputs the step has no branch
     // but the waits, so the loads and arithmetic of the two rows interleave;
     // idle threads and rows without an output do the same work and drop it.
-    // Arm words are fetched a step ahead.
-    uint32_t a0 = __ldg(armc), a1 = __ldg(armc + (size_t)min(1, rows - 1) * X);
-    for (int y = 0; y < rows; y += 2) {
-        const uint32_t n0 = __ldg(armc + (size_t)min(y + 2, rows - 1) * X);
-        const uint32_t n1 = __ldg(armc + (size_t)min(y + 3, rows - 1) * X);
-        const int yo0 = y - wy, yo1 = y + 1 - wy;
-        uint32_t c0[T::DPT], c1[T::DPT], k0, k1;
-        if (y + 1 < Y) {
-            if (!mbar_wait_warp(&full[y % T::RS], (y / T::RS) & 1, limit, a.err)) return;
-            if (!mbar_wait_warp(&full[(y + 1) % T::RS], ((y + 1) / T::RS) & 1, limit, a.err)) return;
-            hsum(y, a0, c0);
-            hsum(y + 1, a1, c1);
-            mbar_arrive(&empty[y % T::RS]);
-            mbar_arrive(&empty[(y + 1) % T::RS]);
-            // Row yo0 reads V down to slot y - 2wy, which shares its ring
-            // slot with y + 2 when wy = 31, so its key is taken before row
-            // y + 1 is pushed.
-            push(y, c0);
-            k0 = vkey(yo0, a0);
-            push(y + 1, c1);
-            k1 = vkey(yo1, a1);
-        } else {
-            // the last input row (when Y is odd) and the rows that only
-            // output; no V beyond V(Y) is ever read
-            if (y < Y) {
-                if (!mbar_wait_warp(&full[y % T::RS], (y / T::RS) & 1, limit, a.err)) return;
-                hsum(y, a0, c0);
-                mbar_arrive(&empty[y % T::RS]);
-                push(y, c0);
-            }
-            k0 = vkey(yo0, a0);
-            k1 = vkey(yo1, a1);
-        }
+    // Arm words are fetched a step ahead. Slabs that lie wholly below D run
+    // without the per-disparity range test.
+    auto sweep = [&](auto part) {
+        constexpr bool kPart = decltype(part)::value;
+        // packed WTA key of output row yo over this thread's disparities
+        auto vkey = [&](int yo, uint32_t am) -> uint32_t {
+            const int up = (am >> 16) & 0xFF, down = am >> 24;
+            Vec vh = myring[((yo + down + 1) & (kRing - 1)) * T::NCT];
+            Vec vl = myring[((yo - up) & (kRing - 1)) * T::NCT];
+            uint32_t best = 0xFFFFFFFFu;
 #pragma unroll
-        for (int o = 1; o < T::G; o <<= 1) {
-            k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, o));
-            k1 = min(k1, __shfl_xor_sync(0xffffffffu, k1, o));
+            for (int k = 0; k < T::DPT; ++k) {
+                const uint32_t kk = ((vget<T::DPT>(vh, k) - vget<T::DPT>(vl, k)) << 8) | (uint32_t)(dg + k);
+                best = (!kPart || dg + k < D) ? min(best, kk) : best;
+            }
+            return best;
+        };
+        uint32_t a0 = __ldg(armc), a1 = __ldg(armc + min(1, rows - 1) * X);
+        for (int y = 0; y < rows; y += 2) {
+            const uint32_t n0 = __ldg(armc + min(y + 2, rows - 1) * X);
+            const uint32_t n1 = __ldg(armc + min(y + 3, rows - 1) * X);
+            const int yo0 = y - wy, yo1 = y + 1 - wy;
+            uint32_t c0[T::DPT], c1[T::DPT], k0, k1;
+            if (y + 1 < Y) {
+                if (!mbar_wait_warp(&full[(y % T::RS) >> 1], (y / T::RS) & 1, limit, a.err)) return;
+                hsum(y, a0, c0);
+                hsum(y + 1, a1, c1);
+                mbar_arrive(&empty[(y % T::RS) >> 1]);
+                // Row yo0 reads V down to slot y - 2wy, which shares its ring
+                // slot with y + 2 when wy = 31, so its key is taken before row
+                // y + 1 is pushed.
+                push(y, c0);
+                k0 = vkey(yo0, a0);
+                push(y + 1, c1);
+                k1 = vkey(yo1, a1);
+            } else {
+                // the last input row (when Y is odd) and the rows that only
+                // output; no V beyond V(Y) is ever read
+                if (y < Y) {
+                    if (!mbar_wait_warp(&full[(y % T::RS) >> 1], (y / T::RS) & 1, limit, a.err)) return;
+                    hsum(y, a0, c0);
+                    mbar_arrive(&empty[(y % T::RS) >> 1]);
+                    push(y, c0);
+                }
+                k0 = vkey(yo0, a0);
+                k1 = vkey(yo1, a1);
+            }
+#pragma unroll
+            for (int o = 1; o < T::G; o <<= 1) {
+                k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, o));
+                k1 = min(k1, __shfl_xor_sync(0xffffffffu, k1, o));
+            }
+            if (g == 0 && valid) {
+                if (yo0 >= 0) atomicMin(key + yo0 * X, k0);
+                if (yo1 >= 0 && y + 1 < rows) atomicMin(key + yo1 * X, k1);
+            }
+            a0 = n0;
+            a1 = n1;
         }
-        if (g == 0 && valid) {
-            if (yo0 >= 0) atomicMin(key + (size_t)yo0 * X, k0);
-            if (yo1 >= 0 && y + 1 < rows) atomicMin(key + (size_t)yo1 * X, k1);
-        }
-        a0 = n0;
-        a1 = n1;
-    }
+    };
+    if (d0 + T::DS <= D)
+        sweep(std::false_type{});
+    else
+        sweep(std::true_type{});
 }
 
 // Tiles of a frame, slab by slab. Slab s (first disparity d0 = s DS) needs
@@ -443,7 +465,7 @@ using T2 = Tile<104, 4, 5, 4, false, 2, 4>;   // wx <= 26, 32-bit prefixes
 using T3 = Tile<96, 4, 7, 4, false, 2, 4>;    // wx <= 29, 32-bit prefixes
 using T4 = Tile<96, 4, 5, 8, true, 4, 4>;     // one consumer thread per column
 using T5 = Tile<64, 4, 5, 8, true, 2, 4>;     // narrow frames
-using T6 = Tile<104, 4, 5, 5, false, 4, 4>;   // wx <= 26, one thread per column and 4 disparities
+using T6 = Tile<104, 4, 5, 4, false, 4, 4>;   // wx <= 26, one thread per column and 4 disparities
 
 template <class T>
 bool fits(const CostAggArgs &a)
