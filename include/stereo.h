@@ -167,14 +167,14 @@ STEREO_API int stereo_stage_ms(stereo_ctx *ctx, float *ms, int n);
 STEREO_API int stereo_last_launch_count(const stereo_ctx *ctx);
 
 /* Tile shapes of the fused cost + aggregation + WTA kernel (columns per base
- * x disparities per CTA, prefix width, disparities per consumer thread):
- * 0: 104x4 16-bit 2, 1: 104x4 16-bit 2 for wx up to 29, 2: 104x4 32-bit 2,
- * 3: 96x4 32-bit 2 for wx up to 29, 4: 96x4 16-bit 4, 5: 64x4 16-bit 2,
- * 6: 104x4 32-bit 4.
+ * x disparities per CTA, row-prefix width); every consumer thread holds one
+ * column and the 4 disparities of its tile:
+ * 0: 104x4 16-bit, 1: 104x4 16-bit for wx up to 29, 2: 104x4 32-bit,
+ * 3: 104x4 32-bit for wx up to 29, 4: 64x4 16-bit.
  * 16-bit row prefixes need (2*wx+1) times the largest matching cost below
  * 2^16. Every shape gives the same result; they differ only in speed. A
  * compute with a shape that does not fit the parameters fails with EINVAL. */
-#define STEREO_NUM_TILES 7
+#define STEREO_NUM_TILES 5
 
 /* Fixes the tile shape used by later computes on this context (-1 = pick
  * automatically from the frame shape and the SM count, the default).

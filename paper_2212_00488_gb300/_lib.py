@@ -181,7 +181,7 @@ def stereo_last_launch_count(ctx):
     return load().stereo_last_launch_count(ctx)
 
 
-NUM_TILES = 7
+NUM_TILES = 5
 
 
 def stereo_set_tile(ctx, tile):

@@ -117,7 +117,7 @@ struct Tile {
     static constexpr int B_LUT = 256 * 8 * 2;
     static constexpr int BYTES = B_BAR + B_RING + B_SX + B_LUT;
     static_assert(DS % DPT == 0 && 32 % G == 0, "the threads of a column sit in adjacent lanes of one warp");
-    static_assert(DPT == 2 || DPT == 4, "ring entries are 8 or 16 bytes");
+    static_assert(DPT == 4, "ring entries are 16 bytes");
     static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
     static_assert(NT <= 1024, "");
     static_assert(RS >= NPW, "every producer warp needs a slot of its own");
@@ -126,13 +126,10 @@ struct Tile {
 };
 
 template <int N> struct VecOf;
-template <> struct VecOf<2> { using type = uint2; };
 template <> struct VecOf<4> { using type = uint4; };
 
 template <int N>
 __device__ __forceinline__ uint32_t &vget(typename VecOf<N>::type &v, int k);
-template <>
-__device__ __forceinline__ uint32_t &vget<2>(uint2 &v, int k) { return k ? v.y : v.x; }
 template <>
 __device__ __forceinline__ uint32_t &vget<4>(uint4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
 
@@ -457,15 +454,31 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_batch_kernel(const __grid_co
     }
 }
 
-// Tile shapes (XS x DS). One CTA per SM; the ring of 64 prefix rows per
-// (column, disparity, base) dominates shared memory.
-using T0 = Tile<104, 4, 5, 8, true, 2, 4>;    // wx <= 26, window sums < 2^16
-using T1 = Tile<104, 4, 7, 6, true, 2, 4>;    // wx <= 29, window sums < 2^16
-using T2 = Tile<104, 4, 5, 4, false, 2, 4>;   // wx <= 26, 32-bit prefixes
-using T3 = Tile<96, 4, 7, 4, false, 2, 4>;    // wx <= 29, 32-bit prefixes
-using T4 = Tile<96, 4, 5, 8, true, 4, 4>;     // one consumer thread per column
-using T5 = Tile<64, 4, 5, 8, true, 2, 4>;     // narrow frames
-using T6 = Tile<104, 4, 5, 4, false, 4, 4>;   // wx <= 26, one thread per column and 4 disparities
+// Tile shapes (XS x DS, KE, RS, 16-bit prefixes, DPT, producer warps). One
+// CTA per SM; the ring of 64 prefix rows per (column, disparity, base)
+// dominates shared memory. Every shape gives the same keys.
+using T0 = Tile<104, 4, 5, 8, true, 4, 8>;    // wx <= 26, window sums < 2^16
+using T1 = Tile<104, 4, 7, 8, true, 4, 8>;    // wx <= 29, window sums < 2^16
+using T2 = Tile<104, 4, 5, 4, false, 4, 4>;   // wx <= 26, 32-bit prefixes
+using T3 = Tile<104, 4, 7, 4, false, 4, 4>;   // wx <= 29, 32-bit prefixes
+using T4 = Tile<64, 4, 5, 8, true, 4, 8>;     // narrow frames, window sums < 2^16
+
+template <class T> struct Tag { using type = T; };
+
+// Calls f(Tag<T>) for the tile shape with the given id; false for an unknown id.
+template <class F>
+bool with_tile(int id, F &&f)
+{
+    switch (id) {
+    case 0: f(Tag<T0>{}); return true;
+    case 1: f(Tag<T1>{}); return true;
+    case 2: f(Tag<T2>{}); return true;
+    case 3: f(Tag<T3>{}); return true;
+    case 4: f(Tag<T4>{}); return true;
+    default: return false;
+    }
+}
+static_assert(kNumTiles == 5, "tile ids 0..4");
 
 template <class T>
 bool fits(const CostAggArgs &a)
@@ -513,87 +526,66 @@ cudaError_t launch_one(const CostAggArgs &a, cudaStream_t s)
 template <class T>
 double estimate(const CostAggArgs &a, int nsm)
 {
-    // time ~ waves x per-CTA work per row (producer entries + consumer cells)
+    // time ~ waves x per-CTA work per row (producer entries + consumer cells);
+    // 32-bit prefixes leave room for fewer row slots and producer warps
     const long ctas = tiles_of<T>(a);
     const long waves = (ctas + nsm - 1) / nsm;
-    const double work = (double)T::DS * (T::XS + T::DS + 2 * a.wx) + 2.0 * T::XS * T::DS;
-    return (double)waves * work * (T::S16 ? 1.0 : 1.05);
+    const double work = (double)T::DS * T::NE + 2.0 * T::XS * T::DS;
+    return (double)waves * work * (T::S16 ? 1.0 : 1.15);
 }
 
 }  // namespace
 
 cudaError_t costagg_setup()
 {
-    cudaError_t e;
-    if ((e = setup_one<T0>()) != cudaSuccess) return e;
-    if ((e = setup_one<T1>()) != cudaSuccess) return e;
-    if ((e = setup_one<T2>()) != cudaSuccess) return e;
-    if ((e = setup_one<T3>()) != cudaSuccess) return e;
-    if ((e = setup_one<T4>()) != cudaSuccess) return e;
-    if ((e = setup_one<T5>()) != cudaSuccess) return e;
-    return setup_one<T6>();
+    cudaError_t e = cudaSuccess;
+    for (int id = 0; id < kNumTiles && e == cudaSuccess; ++id)
+        with_tile(id, [&](auto tag) { e = setup_one<typename decltype(tag)::type>(); });
+    return e;
 }
 
 int costagg_pick(const CostAggArgs &a, int nsm)
 {
     int best = -1;
     double bt = 0;
-    auto consider = [&](int id, bool ok, double est) {
-        if (ok && (best < 0 || est < bt)) { best = id; bt = est; }
-    };
-    consider(0, fits<T0>(a), estimate<T0>(a, nsm));
-    consider(1, fits<T1>(a), estimate<T1>(a, nsm) * 1.01);
-    consider(2, fits<T2>(a), estimate<T2>(a, nsm));
-    consider(3, fits<T3>(a), estimate<T3>(a, nsm) * 1.01);
-    consider(4, fits<T4>(a), estimate<T4>(a, nsm));
-    consider(5, fits<T5>(a), estimate<T5>(a, nsm) * 1.01);
-    consider(6, fits<T6>(a), estimate<T6>(a, nsm));
+    for (int id = 0; id < kNumTiles; ++id)
+        with_tile(id, [&](auto tag) {
+            using T = typename decltype(tag)::type;
+            if (!fits<T>(a)) return;
+            const double est = estimate<T>(a, nsm);
+            if (best < 0 || est < bt) {
+                best = id;
+                bt = est;
+            }
+        });
     return best;
 }
 
 bool costagg_fits(const CostAggArgs &a, int tile)
 {
-    switch (tile) {
-    case 0: return fits<T0>(a);
-    case 1: return fits<T1>(a);
-    case 2: return fits<T2>(a);
-    case 3: return fits<T3>(a);
-    case 4: return fits<T4>(a);
-    case 5: return fits<T5>(a);
-    case 6: return fits<T6>(a);
-    default: return false;
-    }
+    bool ok = false;
+    with_tile(tile, [&](auto tag) { ok = fits<typename decltype(tag)::type>(a); });
+    return ok;
 }
 
 cudaError_t launch_costagg_batch(BatchArgs &b, int tile, int nsm, cudaStream_t s)
 {
     if (b.njobs < 1 || b.njobs > kMaxBatch) return cudaErrorInvalidValue;
-    switch (tile) {
-    case 0: return launch_batch_one<T0>(b, nsm, s);
-    case 1: return launch_batch_one<T1>(b, nsm, s);
-    case 2: return launch_batch_one<T2>(b, nsm, s);
-    case 3: return launch_batch_one<T3>(b, nsm, s);
-    case 4: return launch_batch_one<T4>(b, nsm, s);
-    case 5: return launch_batch_one<T5>(b, nsm, s);
-    case 6: return launch_batch_one<T6>(b, nsm, s);
-    default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = cudaErrorInvalidValue;
+    with_tile(tile, [&](auto tag) { e = launch_batch_one<typename decltype(tag)::type>(b, nsm, s); });
+    return e;
 }
 
 cudaError_t launch_costagg(const CostAggArgs &a, cudaStream_t s)
 {
     if (a.wy > kMaxWy || a.wy < 0 || a.wx < 0 || a.wx > kMaxWx) return cudaErrorInvalidValue;
     const int tile = a.tile >= 0 ? a.tile : costagg_pick(a, a.num_sms);
-    switch (tile) {
-    case 0: return fits<T0>(a) ? launch_one<T0>(a, s) : cudaErrorInvalidValue;
-    case 1: return fits<T1>(a) ? launch_one<T1>(a, s) : cudaErrorInvalidValue;
-    case 2: return fits<T2>(a) ? launch_one<T2>(a, s) : cudaErrorInvalidValue;
-    case 3: return fits<T3>(a) ? launch_one<T3>(a, s) : cudaErrorInvalidValue;
-    case 4: return fits<T4>(a) ? launch_one<T4>(a, s) : cudaErrorInvalidValue;
-    case 5: return fits<T5>(a) ? launch_one<T5>(a, s) : cudaErrorInvalidValue;
-    case 6: return fits<T6>(a) ? launch_one<T6>(a, s) : cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = cudaErrorInvalidValue;
+    with_tile(tile, [&](auto tag) {
+        using T = typename decltype(tag)::type;
+        if (fits<T>(a)) e = launch_one<T>(a, s);
+    });
+    return e;
 }
 
 }  // namespace stereo

@@ -38,7 +38,7 @@ struct CostAggArgs {
 };
 
 // Number of tile shapes of the fused kernel (ids 0 .. kNumTiles-1).
-constexpr int kNumTiles = 7;
+constexpr int kNumTiles = 5;
 int costagg_pick(const CostAggArgs &a, int nsm);
 bool costagg_fits(const CostAggArgs &a, int tile);
 

@@ -101,7 +101,7 @@ def test_paper_size_mix_equals_solo_with_every_fixed_tile_and_graph_update():
     outs_b = _batch(st, frames)
     for a, b in zip(outs, outs_b):
         assert torch.equal(a["disp"], b["disp"])
-    for tile in (0, 2, 5):
+    for tile in (0, 2, 4):
         outs_t = _batch(st, frames[:4], tile=tile)
         for a, b in zip(outs[:4], outs_t):
             assert torch.equal(a["disp"], b["disp"]) and torch.equal(a["dl"], b["dl"])
