@@ -63,13 +63,38 @@ __global__ void downscale_kernel(const uint8_t *__restrict__ g_l, const uint8_t 
 }
 
 // Support data in two passes, each with a halo only along its own axis.
-//  Pass H: rows of kHX pixels (plus wx or 2 pixels each side and one row
+//  Pass H: rows of kHX pixels (plus kMaxWx + 7 pixels each side and one row
 //  above and below): census code and left/right arms; grey | census << 8 goes
 //  to the pixel word, the left/right arms to the low half of the arm words.
-//  Pass V: columns of kVY pixels (plus wy rows above and below): up/down arms
-//  to the high half of the arm words.
+//  Pass V: columns of kVY pixels (plus kMaxWy + 7 rows above and below): up/down
+//  arms to the high half of the arm words.
 // Coordinates of the staged tiles are clamped to the image (border
 // replication, which census reads); the arm scans stop at the real border.
+// Arm length from the staged pixel t (value c) in direction DIR (+1 or -1,
+// element stride S): the number of consecutive pixels k = 1, 2, ... with
+// |I - c| < tc, at most cap. kArmChunk pixels are tested per step, so the
+// loads of a step overlap; the tile holds kArmChunk - 1 pixels beyond each cap.
+constexpr int kArmChunk = 8;
+
+template <int DIR, int S>
+__device__ __forceinline__ int arm_run(const uint8_t *t, int c, int tc, int cap)
+{
+    // |I - c| < tc  <=>  (unsigned)(I - c + tc - 1) < 2 tc - 1
+    const int off = tc - 1 - c;
+    const unsigned lim = tc > 0 ? (unsigned)(2 * tc - 1) : 0u;   // tc = 0: nothing is similar
+    int n = 0;
+    while (n < cap) {
+        const uint8_t *p = t + DIR * (n + 1) * S;
+        uint32_t m = 0;
+#pragma unroll
+        for (int j = 0; j < kArmChunk; ++j) m |= (uint32_t)((unsigned)(p[DIR * j * S] + off) < lim) << j;
+        const int run = __ffs(~m) - 1;           // similar pixels at the head of the chunk
+        n = min(n + run, cap);
+        if (run < kArmChunk) break;
+    }
+    return n;
+}
+
 constexpr int kHX = 256;   // pass H: outputs per row tile
 constexpr int kHY = 4;     // pass H: rows per CTA
 constexpr int kVX = 32;    // pass V: columns per CTA
@@ -90,7 +115,7 @@ __global__ void __launch_bounds__(kSupNT) support_h_kernel(
     uint16_t *arm = reinterpret_cast<uint16_t *>(blockIdx.z ? arm_r : arm_l);
     uint16_t *armc = reinterpret_cast<uint16_t *>(blockIdx.z ? armc_r : armc_l);
     uint32_t *key = blockIdx.z ? key_r : key_l;
-    const int hx = max(wx, 2);
+    const int hx = kMaxWx + kArmChunk - 1;      // >= 2, the census reach
     const int TW = kHX + 2 * hx, TH = kHY + 2;
     const int x0 = blockIdx.x * kHX, y0 = blockIdx.y * kHY;
     if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *err = 0u;
@@ -117,9 +142,8 @@ __global__ void __launch_bounds__(kSupNT) support_h_kernel(
             uint32_t code = 0;
 #pragma unroll
             for (int k = 0; k < 6; ++k) code |= (uint32_t)(t[cdy[k] * TW + cdx[k]] < c) << k;
-            int hm = 0, hp = 0;
-            while (hm < wx && x - hm - 1 >= 0 && abs((int)t[-(hm + 1)] - c) < tc) ++hm;
-            while (hp < wx && x + hp + 1 < X && abs((int)t[hp + 1] - c) < tc) ++hp;
+            const int hm = arm_run<-1, 1>(t, c, tc, min(wx, x));
+            const int hp = arm_run<1, 1>(t, c, tc, min(wx, X - 1 - x));
             const size_t idx = (size_t)y * X + x;
             pix[idx] = (uint32_t)c | (code << 8);
             const uint16_t h = (uint16_t)(hm | (hp << 8));
@@ -139,7 +163,7 @@ __global__ void __launch_bounds__(kSupNT) support_v_kernel(
     const uint8_t *g = blockIdx.z ? g_r : g_l;
     uint16_t *arm = reinterpret_cast<uint16_t *>(blockIdx.z ? arm_r : arm_l);
     uint16_t *armc = reinterpret_cast<uint16_t *>(blockIdx.z ? armc_r : armc_l);
-    const int hy = max(wy, 1);
+    const int hy = kMaxWy + kArmChunk - 1;
     const int TH = kVY + 2 * hy;
     const int x0 = blockIdx.x * kVX, y0 = blockIdx.y * kVY;
     const int tx = threadIdx.x % kVX, tq = threadIdx.x / kVX;     // kSupNT / kVX threads per column
@@ -153,9 +177,8 @@ __global__ void __launch_bounds__(kSupNT) support_v_kernel(
         if (y >= Y) break;
         const uint8_t *t = tile + (oy + hy) * kVX + tx;
         const int c = t[0];
-        int vm = 0, vp = 0;
-        while (vm < wy && y - vm - 1 >= 0 && abs((int)t[-(vm + 1) * kVX] - c) < tc) ++vm;
-        while (vp < wy && y + vp + 1 < Y && abs((int)t[(vp + 1) * kVX] - c) < tc) ++vp;
+        const int vm = arm_run<-1, kVX>(t, c, tc, min(wy, y));
+        const int vp = arm_run<1, kVX>(t, c, tc, min(wy, Y - 1 - y));
         const uint16_t v = (uint16_t)(vm | (vp << 8));
         arm[2 * ((size_t)y * X + x) + 1] = v;
         // the fused kernel reads the up/down arms of output row y in row y + wy
@@ -204,7 +227,8 @@ cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix
                            uint32_t *key_l, uint32_t *key_r, uint32_t *err, int X, int Y, int wx, int wy,
                            int tc, cudaStream_t s)
 {
-    const int hx = wx > 2 ? wx : 2, hy = wy > 1 ? wy : 1;
+    if (wx > kMaxWx || wy > kMaxWy) return cudaErrorInvalidValue;
+    const int hx = kMaxWx + kArmChunk - 1, hy = kMaxWy + kArmChunk - 1;
     dim3 gh((X + kHX - 1) / kHX, (Y + kHY - 1) / kHY, 2);
     support_h_kernel<<<gh, kSupNT, (size_t)(kHX + 2 * hx) * (kHY + 2), s>>>(
         g_l, g_r, pix_l, pix_r, arm_l, arm_r, armc_l, armc_r, key_l, key_r, err, X, Y, wx, tc);
