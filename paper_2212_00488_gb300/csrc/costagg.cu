@@ -15,24 +15,26 @@
 //    C^R(x, y, d) = C^L(x+d, y, d), and for d in the slab the right windows
 //    land inside [x0-wx, x0+XS+DS-1+wx), next to the left windows.
 //
-// Warp roles (the row buffers between them form a ring of RS slots guarded
-// by full/empty mbarriers):
-//  * Producer warp p (one per disparity d = d0 + p), for each input row y:
-//      S[i] = sum_{j<i} C^L(x0 - wx + j, y, d)      (row prefix, exact uint32)
+// Warp roles (the row buffers between them form a ring of RS slots; rows 2k
+// and 2k+1 share one full and one empty mbarrier):
+//  * Producer warp p (NPW of them) fills rows y = p, p + NPW, ...: for each
+//    disparity d = d0 + q of the slab, the exclusive row prefix
+//      S_q[i] = sum_{j<i} C^L(x0 - wx + j, y, d)                  (Eq. 7)
 //    with C^L = P when the pixel or its match x - d is outside the image.
-//    Each lane sums KE consecutive costs, a warp scan adds the lanes' totals.
-//    The producers also stage the arm rows the consumers need.
-//  * Consumer thread (base, column, disparity), for each row:
-//      CA_x = S[hi] - S[lo] over the pixel's own left/right arms   (Eq. 7)
+//    Each lane sums KE consecutive costs (one table lookup each: the AD and
+//    census terms of Eqs. 3-5 combined), a warp scan adds the lanes' totals.
+//    Prefixes are exact modulo 2^16 or 2^32 (16-bit only when every
+//    horizontal window sum is below 2^16, checked on the host).
+//  * Consumer thread (base, column) holds the slab's DS = 4 disparities and
+//    takes two rows per step:
+//      CA_x = S_q[hi] - S_q[lo] over the pixel's own left/right arms  (Eq. 7)
 //      V(y+1) = V(y) + CA_x  -> ring slot (y+1) mod 64
-//      CA(yo) = V(yo + down + 1) - V(yo - up), yo = y - wy        (Eq. 8)
-//      key = min over d of (CA << 8 | d)                           (Eq. 9)
-//    The DS disparities of a column sit in adjacent lanes, so the slab's
-//    minimum is a few shuffles; the minimum over slabs is one atomicMin per
-//    pixel and base. The packed key keeps the smallest d among equal costs,
-//    the tie rule of Step 5.
-// All sums are modular uint32: differences are exact because every window sum
-// is below 2^24 (checked on the host).
+//      CA(yo) = V(yo + down + 1) - V(yo - up), yo = y - wy          (Eq. 8)
+//      key = min over d of (CA << 8 | d)                             (Eq. 9)
+//    The minimum over slabs is one atomicMin per pixel and base. The packed
+//    key keeps the smallest d among equal costs, the tie rule of Step 5.
+// Vertical sums are modular uint32: differences are exact because every
+// window sum is below 2^24 (checked on the host).
 //
 // Every wait on an mbarrier is bounded: after a.wait_limit polls the thread
 // sets a.err and returns, so a broken hand-off ends the kernel with an error
