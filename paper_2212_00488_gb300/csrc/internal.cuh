@@ -77,6 +77,13 @@ cudaError_t diff_run(const DiffArgs &a, cudaStream_t s);
 // Launchers (each returns the launch error, cudaSuccess on success).
 cudaError_t launch_grey(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t *g_l, uint8_t *g_r,
                         int W, int H, cudaStream_t s);
+// Grey of both images and its Eq. 2 downscale, with the full-resolution grey
+// of the left image (what the scale-up reads): one launch when W is a
+// multiple of 4 and the RGB rows are word-aligned (gf_r is then not written),
+// else grey_kernel and downscale_kernel. Adds the kernels launched to
+// *launches.
+cudaError_t launch_grey_down(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t *gf_l, uint8_t *gf_r,
+                            uint8_t *s_l, uint8_t *s_r, int W, int H, cudaStream_t s, int *launches);
 cudaError_t launch_downscale(const uint8_t *g_l, const uint8_t *g_r, uint8_t *s_l, uint8_t *s_r,
                              int W, int H, cudaStream_t s);
 // Also presets the WTA keys of both bases to ~0 and clears the fused

@@ -62,6 +62,86 @@ __global__ void downscale_kernel(const uint8_t *__restrict__ g_l, const uint8_t 
     s[(size_t)y * X + x] = (uint8_t)((sum + 4) / 9);
 }
 
+// Grey conversion and Eq. 2 downscale in one pass (the downscaling path, for
+// W a multiple of 4 and 4-byte aligned RGB rows). A CTA makes a kGDX x kGDY
+// tile of downscaled pixels of one image: it converts the full-res pixels
+// [2 x0 - 4, 2 x0 + 2 kGDX + 4) of rows 2 y0 - 1 .. 2 y0 + 2 kGDY - 1 (row and
+// column coordinates clamped, as in downscale_kernel) four at a time from
+// three aligned words, keeps them in shared memory, writes the left image's
+// full-res grey of its interior (the scale-up reads it) and the 3x3 means.
+// Same arithmetic as grey_kernel followed by downscale_kernel.
+constexpr int kGDX = 64, kGDY = 4;
+constexpr int kGRW = 2 * kGDX + 8, kGRH = 2 * kGDY + 1;   // region: 136 x 9 pixels
+
+__global__ void __launch_bounds__(kGDX * kGDY) grey_down_kernel(
+    const uint8_t *__restrict__ rgb_l, const uint8_t *__restrict__ rgb_r, uint8_t *__restrict__ gf_l,
+    uint8_t *__restrict__ s_l, uint8_t *__restrict__ s_r, int W, int H)
+{
+    __shared__ __align__(4) uint8_t reg[kGRH][kGRW];
+    const bool right = blockIdx.z != 0;
+    const uint8_t *rgb = right ? rgb_r : rgb_l;
+    uint8_t *s = right ? s_r : s_l;
+    const int X = W / 2, Y = H / 2;
+    const int x0 = blockIdx.x * kGDX, y0 = blockIdx.y * kGDY;
+    const int fx0 = 2 * x0 - 4, fy0 = 2 * y0 - 1;     // full-res origin of the region
+    constexpr int kGroups = kGRW / 4, kN = kGroups * kGRH, kNT = kGDX * kGDY;
+    constexpr int kPer = (kN + kNT - 1) / kNT;                 // groups per thread
+    // all loads of the thread first, so that they are in flight together
+    uint32_t w[kPer][3];
+    bool inside[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = threadIdx.x + k * kNT;
+        const int gx = i % kGroups, ry = i / kGroups;
+        const int fx = fx0 + 4 * gx;
+        inside[k] = i < kN && fx >= 0 && fx + 4 <= W;
+        if (inside[k]) {
+            const uint32_t *p = reinterpret_cast<const uint32_t *>(
+                rgb + ((size_t)min(max(fy0 + ry, 0), H - 1) * W + fx) * 3);
+            w[k][0] = __ldg(p);
+            w[k][1] = __ldg(p + 1);
+            w[k][2] = __ldg(p + 2);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = threadIdx.x + k * kNT;
+        if (i >= kN) break;
+        const int gx = i % kGroups, ry = i / kGroups;
+        const int fx = fx0 + 4 * gx, fy = fy0 + ry;
+        uint32_t q;
+        if (inside[k]) {
+            const uint32_t w0 = w[k][0], w1 = w[k][1], w2 = w[k][2];
+            q = luma(w0 & 0xFF, (w0 >> 8) & 0xFF, (w0 >> 16) & 0xFF) |
+                luma(w0 >> 24, w1 & 0xFF, (w1 >> 8) & 0xFF) << 8 |
+                luma((w1 >> 16) & 0xFF, w1 >> 24, w2 & 0xFF) << 16 |
+                luma((w2 >> 8) & 0xFF, (w2 >> 16) & 0xFF, w2 >> 24) << 24;
+        } else {
+            // a group across the left or right border: clamped pixel by pixel
+            const uint8_t *row = rgb + (size_t)min(max(fy, 0), H - 1) * 3 * W;
+            q = 0;
+            for (int c = 0; c < 4; ++c) {
+                const uint8_t *p = row + 3 * min(max(fx + c, 0), W - 1);
+                q |= luma(__ldg(p), __ldg(p + 1), __ldg(p + 2)) << (8 * c);
+            }
+        }
+        *reinterpret_cast<uint32_t *>(&reg[ry][4 * gx]) = q;
+        // interior: columns [2 x0, 2 x0 + 2 kGDX), rows [2 y0, 2 y0 + 2 kGDY)
+        if (!right && gx >= 1 && gx <= 2 * kGDX / 4 && ry >= 1 && fx < W && fy < H)
+            *reinterpret_cast<uint32_t *>(gf_l + (size_t)fy * W + fx) = q;
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % kGDX, ly = threadIdx.x / kGDX;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= X || y >= Y) return;
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sum += reg[2 * ly + j][2 * lx + 3 + i];
+    s[(size_t)y * X + x] = (uint8_t)((sum + 4) / 9);
+}
+
 // Support data in two passes, each with a halo only along its own axis.
 //  Pass H: rows of kHX pixels (plus kMaxWx + 7 pixels each side and one row
 //  above and below): census code and left/right arms; grey | census << 8 goes
@@ -219,6 +299,26 @@ cudaError_t launch_downscale(const uint8_t *g_l, const uint8_t *g_r, uint8_t *s_
     int X = W / 2, Y = H / 2;
     dim3 grid((X + 127) / 128, Y, 2);
     downscale_kernel<<<grid, 128, 0, s>>>(g_l, g_r, s_l, s_r, W, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grey_down(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t *gf_l, uint8_t *gf_r,
+                            uint8_t *s_l, uint8_t *s_r, int W, int H, cudaStream_t s, int *launches)
+{
+    const int X = W / 2, Y = H / 2;
+    if (X < 1 || Y < 1) return cudaErrorInvalidValue;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(rgb_l) | reinterpret_cast<uintptr_t>(rgb_r) |
+                           reinterpret_cast<uintptr_t>(gf_l)) & 3) == 0;
+    if (W % 4 != 0 || !aligned) {
+        // rows not word-aligned: the two separate passes
+        *launches += 2;
+        cudaError_t e = launch_grey(rgb_l, rgb_r, gf_l, gf_r, W, H, s);
+        return e != cudaSuccess ? e : launch_downscale(gf_l, gf_r, s_l, s_r, W, H, s);
+    }
+    // W a multiple of 4: every interior group of four lies inside the row
+    dim3 grid((X + kGDX - 1) / kGDX, ((H + 1) / 2 + kGDY - 1) / kGDY, 2);
+    grey_down_kernel<<<grid, kGDX * kGDY, 0, s>>>(rgb_l, rgb_r, gf_l, s_l, s_r, W, H);
+    *launches += 1;
     return cudaGetLastError();
 }
 

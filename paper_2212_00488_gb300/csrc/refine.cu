@@ -170,24 +170,40 @@ __device__ __forceinline__ float rowpass(const float *__restrict__ dp, const uin
 // Step 8: bilateral estimation along x, linear along y; full-resolution
 // disparity units (x2). Odd output columns between two low-res pixels whose
 // disparities differ by more than T take the side whose low-res brightness is
-// strictly closer to the full-res pixel's (else the right side).
+// strictly closer to the full-res pixel's (else the right side). One thread
+// makes the 2x2 outputs (2x..2x+1, 2y..2y+1) of low-res position (x, y), so
+// each row pass is computed once.
+template <bool kPairs>
 __global__ void upscale_kernel(const float *__restrict__ dp, const uint8_t *__restrict__ gs,
                                const uint8_t *__restrict__ gf, int X, int Y, int W, int H, int T,
                                float *__restrict__ out)
 {
-    const int xo = blockIdx.x * blockDim.x + threadIdx.x;
-    const int yo = blockIdx.y;
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int by = blockIdx.y;
+    const int xo = 2 * bx, yo = 2 * by;
     if (xo >= W || yo >= H) return;
-    const int y = yo >> 1;
-    float v;
-    if ((yo & 1) == 0 || y + 1 >= Y) {
-        v = rowpass(dp, gs, gf, X, W, T, xo, min(y, Y - 1));
-    } else {
-        const float r0 = rowpass(dp, gs, gf, X, W, T, xo, y);
-        const float r1 = rowpass(dp, gs, gf, X, W, T, xo, y + 1);
-        v = __fmul_rn(0.5f, __fadd_rn(r0, r1));
+    const int yc = min(by, Y - 1);
+    float e0 = rowpass(dp, gs, gf, X, W, T, xo, yc);
+    float o0 = xo + 1 < W ? rowpass(dp, gs, gf, X, W, T, xo + 1, yc) : 0.f;
+    float e1 = e0, o1 = o0;
+    if (by + 1 < Y) {
+        const float e2 = rowpass(dp, gs, gf, X, W, T, xo, by + 1);
+        const float o2 = xo + 1 < W ? rowpass(dp, gs, gf, X, W, T, xo + 1, by + 1) : 0.f;
+        e1 = __fmul_rn(0.5f, __fadd_rn(e0, e2));
+        o1 = __fmul_rn(0.5f, __fadd_rn(o0, o2));
     }
-    out[(size_t)yo * W + xo] = v;
+    float *r0 = out + (size_t)yo * W + xo;
+    if (kPairs) {                                   // W even: 8-byte aligned pairs
+        *reinterpret_cast<float2 *>(r0) = make_float2(e0, o0);
+        if (yo + 1 < H) *reinterpret_cast<float2 *>(r0 + W) = make_float2(e1, o1);
+    } else {
+        r0[0] = e0;
+        if (xo + 1 < W) r0[1] = o0;
+        if (yo + 1 < H) {
+            r0[W] = e1;
+            if (xo + 1 < W) r0[W + 1] = o1;
+        }
+    }
 }
 
 size_t refine_smem(int X) { return (size_t)X * (2 * sizeof(int) + 7) + 32 * sizeof(int); }
@@ -212,8 +228,12 @@ cudaError_t launch_refine(const uint32_t *key_l, const uint32_t *key_r, const ui
 cudaError_t launch_upscale(const float *dplus, const uint8_t *grey_low, const uint8_t *grey_full,
                            int X, int Y, int W, int H, int T, float *out, cudaStream_t s)
 {
-    dim3 grid((W + 255) / 256, H);
-    upscale_kernel<<<grid, 256, 0, s>>>(dplus, grey_low, grey_full, X, Y, W, H, T, out);
+    dim3 grid(((W + 1) / 2 + 127) / 128, (H + 1) / 2);
+    const bool pairs = W % 2 == 0 && (reinterpret_cast<uintptr_t>(out) & 7) == 0;
+    if (pairs)
+        upscale_kernel<true><<<grid, 128, 0, s>>>(dplus, grey_low, grey_full, X, Y, W, H, T, out);
+    else
+        upscale_kernel<false><<<grid, 128, 0, s>>>(dplus, grey_low, grey_full, X, Y, W, H, T, out);
     return cudaGetLastError();
 }
 

@@ -240,11 +240,11 @@ cudaError_t run_stage(stereo_ctx *c, int stage, cudaStream_t s)
     const bool ds = c->p.downscale != 0;
     switch (stage) {
     case STEREO_STAGE_SCALEDOWN: {
-        cudaError_t e = launch_grey(c->in_l, c->in_r, c->gf[0], c->gf[1], c->W, c->H, s);
+        if (ds)
+            return launch_grey_down(c->in_l, c->in_r, c->gf[0], c->gf[1], c->gs[0], c->gs[1], c->W, c->H, s,
+                                    &c->launches);
         c->launches++;
-        if (e != cudaSuccess || !ds) return e;
-        c->launches++;
-        return launch_downscale(c->gf[0], c->gf[1], c->gs[0], c->gs[1], c->W, c->H, s);
+        return launch_grey(c->in_l, c->in_r, c->gf[0], c->gf[1], c->W, c->H, s);
     }
     case STEREO_STAGE_SUPPORT:
         c->launches += 2;
@@ -670,10 +670,11 @@ CostAggArgs frame_args(const stereo_ctx *c, const FrameWs &f)
 
 cudaError_t batch_prep(stereo_ctx *c, const stereo_job &j, const FrameWs &f, cudaStream_t s, int &launches)
 {
-    cudaError_t e = launch_grey(j.left_rgb, j.right_rgb, f.gf[0], f.gf[1], f.W, f.H, s);
-    launches++;
-    if (e == cudaSuccess && c->p.downscale) {
-        e = launch_downscale(f.gf[0], f.gf[1], f.gs[0], f.gs[1], f.W, f.H, s);
+    cudaError_t e;
+    if (c->p.downscale) {
+        e = launch_grey_down(j.left_rgb, j.right_rgb, f.gf[0], f.gf[1], f.gs[0], f.gs[1], f.W, f.H, s, &launches);
+    } else {
+        e = launch_grey(j.left_rgb, j.right_rgb, f.gf[0], f.gf[1], f.W, f.H, s);
         launches++;
     }
     if (e == cudaSuccess) {
