@@ -152,9 +152,19 @@ __global__ void __launch_bounds__(kGDX * kGDY) grey_down_kernel(
 // replication, which census reads); the arm scans stop at the real border.
 // Arm length from the staged pixel t (value c) in direction DIR (+1 or -1,
 // element stride S): the number of consecutive pixels k = 1, 2, ... with
-// |I - c| < tc, at most cap. kArmChunk pixels are tested per step, so the
-// loads of a step overlap; the tile holds kArmChunk - 1 pixels beyond each cap.
+// |I - c| < tc, at most cap. Most arms are short, so the first step tests 4
+// pixels and later steps 8; the loads of a step overlap. The tile holds
+// kArmChunk - 1 pixels beyond each cap.
 constexpr int kArmChunk = 8;
+
+template <int DIR, int S, int N>
+__device__ __forceinline__ int arm_chunk(const uint8_t *p, int off, unsigned lim)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) m |= (uint32_t)((unsigned)(p[DIR * j * S] + off) < lim) << j;
+    return __ffs(~m) - 1;                        // similar pixels at the head of the chunk
+}
 
 template <int DIR, int S>
 __device__ __forceinline__ int arm_run(const uint8_t *t, int c, int tc, int cap)
@@ -162,13 +172,12 @@ __device__ __forceinline__ int arm_run(const uint8_t *t, int c, int tc, int cap)
     // |I - c| < tc  <=>  (unsigned)(I - c + tc - 1) < 2 tc - 1
     const int off = tc - 1 - c;
     const unsigned lim = tc > 0 ? (unsigned)(2 * tc - 1) : 0u;   // tc = 0: nothing is similar
-    int n = 0;
+    if (cap <= 0) return 0;
+    int run = arm_chunk<DIR, S, 4>(t + DIR * S, off, lim);
+    int n = min(run, cap);
+    if (run < 4) return n;
     while (n < cap) {
-        const uint8_t *p = t + DIR * (n + 1) * S;
-        uint32_t m = 0;
-#pragma unroll
-        for (int j = 0; j < kArmChunk; ++j) m |= (uint32_t)((unsigned)(p[DIR * j * S] + off) < lim) << j;
-        const int run = __ffs(~m) - 1;           // similar pixels at the head of the chunk
+        run = arm_chunk<DIR, S, kArmChunk>(t + DIR * (n + 1) * S, off, lim);
         n = min(n + run, cap);
         if (run < kArmChunk) break;
     }
