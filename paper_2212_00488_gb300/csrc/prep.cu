@@ -187,7 +187,7 @@ __device__ __forceinline__ int arm_run(const uint8_t *t, int c, int tc, int cap)
 constexpr int kHX = 256;   // pass H: outputs per row tile
 constexpr int kHY = 4;     // pass H: rows per CTA
 constexpr int kVX = 32;    // pass V: columns per CTA
-constexpr int kVY = 32;    // pass V: outputs per column tile
+constexpr int kVY = 16;    // pass V: outputs per column tile
 constexpr int kSupNT = 256;
 
 __global__ void __launch_bounds__(kSupNT) support_h_kernel(
