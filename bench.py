@@ -412,6 +412,8 @@ def run_ours(args):
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak_ops = sm_count * LANES_PER_SM * sm_mhz * 1e6
         achieved = OPS_PER_CELL * cells / t_hot
+        # measured rates of the operations the count is made of (after the timed region)
+        int_ops, popc_s, lds_bps = _lib.stereo_measure_peaks(dev.index)
         line = {
             "metric": METRIC,
             "value": fps,
@@ -440,6 +442,10 @@ def run_ours(args):
                          "traffic_unit": "bytes per launch (dram read + write, ncu)",
                          "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz (issue limit, "
                                         f"max clock from {src} peaks)",
+                         "measured": {"int32_add_xor_min_tops": int_ops / 1e12, "popc_tops": popc_s / 1e12,
+                                      "lds_tb_per_s": lds_bps / 1e12,
+                                      "frac_of_measured_int32": achieved / int_ops,
+                                      "source": "stereo_measure_peaks microbenchmarks on this GPU"},
                          "ops_per_cell": OPS_PER_CELL, "cells_per_launch": cells,
                          "kernel_ms": stage_ms[_lib.STAGE_COSTAGG], "frames_timed": nframes,
                          "tile": _lib.stereo_get_tile(st.ctx, W_FULL, H_FULL, DMAX)},

@@ -287,6 +287,18 @@ STEREO_API int stereo_compute_noalloc(const stereo_params *params, const uint8_t
                                       uint8_t *dl_out, uint8_t *dr_out, uint8_t *gcp_out, void *stream,
                                       char *err, size_t err_len);
 
+/* Throughput microbenchmarks for the roofline of the fused kernel (no
+ * counterpart in the paper): 32-bit integer add/xor/min, population count and
+ * 16-byte shared-memory loads, each as independent chains with every SM of
+ * the device full of warps, timed with CUDA events (about 10 ms in all).
+ *  device: CUDA device index.
+ *  int_ops_per_s, popc_per_s, lds_bytes_per_s: results (operations or bytes
+ *    per second, whole device).
+ * Allocates a few KB of device memory for the duration of the call. Returns
+ * STEREO_OK, STEREO_EINVAL for a null pointer, STEREO_ECUDA on a CUDA error. */
+STEREO_API int stereo_measure_peaks(int device, double *int_ops_per_s, double *popc_per_s,
+                                    double *lds_bytes_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,8 @@ _SIGNATURES = {
                                   _vp, _vp, _vp, _vp]),
     "stereo_compute_noalloc": (_i, [ctypes.POINTER(stereo_params), _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp,
                                     _vp, ctypes.c_char_p, ctypes.c_size_t]),
+    "stereo_measure_peaks": (_i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -236,3 +238,10 @@ def stereo_diff_backward(ctx, B, W, H, D, left, right, left_u8, right_u8, theta,
     return check(ctx, load().stereo_diff_backward(ctx, B, W, H, D, left, right, left_u8, right_u8, theta, tau,
                                                   dhat, stats, grad_dhat, grad_left, grad_right, grad_theta,
                                                   stream or None))
+
+
+def stereo_measure_peaks(device=0):
+    """Measured whole-device rates: (int32 add/xor/min ops/s, popc/s, shared-memory load bytes/s)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(None, load().stereo_measure_peaks(device, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libstereo.so")
 BUILD = os.path.join(ROOT, "_build", "stereo")
-SOURCES = ["stereo_api.cu", "prep.cu", "costagg.cu", "refine.cu", "noalloc.cu", "diff.cu"]
+SOURCES = ["stereo_api.cu", "prep.cu", "costagg.cu", "refine.cu", "noalloc.cu", "diff.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
