@@ -69,6 +69,12 @@ typedef struct {
     int downscale;    /* 1: K = 2, m = 1 mean-pool with Dmax halved (Sec. III-A); 0: none */
     int cost_scale;   /* integer cost mode: each term is round(cost_scale * value); 512.
                          (2*wx+1)*(2*wy+1)*(AD(255)+MC(6)) must stay below 2^24. */
+    int fill_mode;    /* non-GCP fill between the nearest GCPs a (left, distance i) and b
+                         (right, distance j), Sec. III-E: 0 = the paper's bilateral
+                         estimation (default); 1 = the closer GCP (Fig. 5a prior art; the
+                         left one when i < j, else the right one); 2 = the smaller
+                         disparity (Fig. 5b prior art). One-sided and empty rows are
+                         filled alike in every mode. */
 } stereo_params;
 
 typedef struct stereo_ctx stereo_ctx;

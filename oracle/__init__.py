@@ -51,7 +51,7 @@ def lib():
         L.oracle_wta_f64.restype = _int
         L.oracle_crosscheck.argtypes = [_u8p, _u8p, _int, _int, _u8p]
         L.oracle_median3.argtypes = [_u8p, _int, _int, _u8p]
-        L.oracle_fill.argtypes = [_u8p, _u8p, _u8p, _int, _int, _int, _f32p]
+        L.oracle_fill.argtypes = [_u8p, _u8p, _u8p, _int, _int, _int, _int, _f32p]
         L.oracle_upscale.argtypes = [_f32p, _u8p, _u8p, _int, _int, _int, _int, _int, _f32p]
         L.oracle_diff.argtypes = [_f64p, _f64p] + [_u8p] * 6 + [_int] * 3 + [_f64p, _dbl, _f64p,
                                                                            ctypes.c_void_p, ctypes.c_void_p,
@@ -72,6 +72,7 @@ class Params:
     t_fill: int = 3       # T of the bilateral estimation
     downscale: int = 1    # 1: K = 2, m = 1 mean-pool and Dmax halved; 0: none
     cost_scale: int = 512  # integer mode: each cost term is round(scale * value)
+    fill_mode: int = 0    # 0 bilateral estimation; 1 closer GCP (Fig. 5a); 2 smaller disparity (Fig. 5b)
 
 
 def _c(a, dtype):
@@ -180,11 +181,13 @@ def median3(d):
     return out
 
 
-def fill(dm, gcp, g, T=3):
+def fill(dm, gcp, g, T=3, mode=0):
+    """Sec. III-E fill of non-GCPs; mode 0 bilateral estimation, 1 the closer
+    GCP (Fig. 5a), 2 the smaller disparity (Fig. 5b)."""
     dm = _c(dm, np.uint8)
     Y, X = dm.shape
     out = np.empty((Y, X), np.float32)
-    lib().oracle_fill(dm, _c(gcp, np.uint8), _c(g, np.uint8), X, Y, T, out)
+    lib().oracle_fill(dm, _c(gcp, np.uint8), _c(g, np.uint8), X, Y, T, mode, out)
     return out
 
 
@@ -234,7 +237,7 @@ def pipeline(left_rgb, right_rgb, dmax: int, p: Params = Params()) -> Result:
     dr = wta_int(gr, cr, gl, cl, ar, D, +1, p)
     gcp = crosscheck(dl, dr)
     dm = median3(dl)
-    dplus = fill(dm, gcp, gl, p.t_fill)
+    dplus = fill(dm, gcp, gl, p.t_fill, p.fill_mode)
     if p.downscale:
         disp = upscale(dplus, gl, gl_full, p.t_fill)
     else:

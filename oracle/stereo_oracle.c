@@ -331,9 +331,14 @@ void oracle_median3(const uint8_t *dl, int X, int Y, uint8_t *dm)
  *  - |a - b| > T: a when L(x - i) is strictly closer in brightness to L(x)
  *    than L(x + j), otherwise b.
  *  - One side only: that side's disparity. Neither side: 0 (paper silent).
- * GCP pixels keep Dm. Output is float [Y][X] in processed-resolution units. */
+ * GCP pixels keep Dm. Output is float [Y][X] in processed-resolution units.
+ * mode selects the fill between two GCPs: 0 the bilateral estimation above
+ * (the paper's method); 1 and 2 the two prior-art approaches Sec. III-E
+ * describes before it (Fig. 5): 1 takes the GCP nearer in distance (the left
+ * one only when strictly nearer: the paper is silent on a tie), 2 takes the
+ * smaller of the two disparities (the occluded side). */
 void oracle_fill(const uint8_t *dm, const uint8_t *gcp, const uint8_t *g, int X, int Y, int T,
-                 float *out)
+                 int mode, float *out)
 {
     for (int y = 0; y < Y; ++y)
         for (int x = 0; x < X; ++x) {
@@ -345,7 +350,11 @@ void oracle_fill(const uint8_t *dm, const uint8_t *gcp, const uint8_t *g, int X,
             float v;
             if (i && j) {
                 int a = dm[r + x - i], b = dm[r + x + j];
-                if (absi(a - b) <= T) {
+                if (mode == 1) {
+                    v = (float)(i < j ? a : b);
+                } else if (mode == 2) {
+                    v = (float)(a < b ? a : b);
+                } else if (absi(a - b) <= T) {
                     v = (float)(a * j + b * i) / (float)(i + j);
                 } else {
                     int ga = absi((int)g[r + x - i] - (int)g[r + x]);

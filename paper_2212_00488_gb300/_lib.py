@@ -52,6 +52,7 @@ class stereo_params(ctypes.Structure):
         ("t_fill", ctypes.c_int),
         ("downscale", ctypes.c_int),
         ("cost_scale", ctypes.c_int),
+        ("fill_mode", ctypes.c_int),
     ]
 
 

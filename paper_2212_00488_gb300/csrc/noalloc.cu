@@ -68,6 +68,7 @@ extern "C" int stereo_compute_noalloc(const stereo_params *params, const uint8_t
         return say(err, err_len, STEREO_EINVAL, "left, right and disp_out must not be NULL");
     if (!(p.lambda_ad > 0) || !(p.lambda_mc > 0) || p.tc < 0 || p.tc > 256 || p.wx < 0 || p.wx > kMaxWx ||
         p.wy < 0 || p.wy > kMaxWy || p.t_fill < 0 || p.t_fill > 255 || (p.downscale != 0 && p.downscale != 1) ||
+        p.fill_mode < 0 || p.fill_mode > 2 ||
         p.cost_scale < 1 || p.cost_scale > (1 << 20))
         return say(err, err_len, STEREO_EINVAL, "parameter out of range");
     const double pmax = p.cost_scale * ((1.0 - std::exp(-1.0 / p.lambda_ad)) + (1.0 - std::exp(-6.0 / p.lambda_mc))) + 1.0;
@@ -148,7 +149,7 @@ extern "C" int stereo_compute_noalloc(const stereo_params *params, const uint8_t
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         a.num_sms = nsm;
         if ((e = launch_costagg(a, s)) == cudaSuccess &&
-            (e = launch_refine(u32(o_key[0]), u32(o_key[1]), u8(o_gs[0]), X, Y, p.t_fill, dl_out, dr_out, gcp_out,
+            (e = launch_refine(u32(o_key[0]), u32(o_key[1]), u8(o_gs[0]), X, Y, p.t_fill, p.fill_mode, dl_out, dr_out, gcp_out,
                                u8(o_dm), dplus, s)) == cudaSuccess && ds)
             e = launch_upscale(dplus, u8(o_gs[0]), u8(o_gf[0]), X, Y, W, H, p.t_fill, disp_out, s);
     }

@@ -72,7 +72,7 @@ __device__ int scan_min_excl_rev(int v, int *sh)
 // One CTA per processed row y.
 __global__ void __launch_bounds__(kRefNT) refine_kernel(
     const uint32_t *__restrict__ key_l, const uint32_t *__restrict__ key_r,
-    const uint8_t *__restrict__ grey, int X, int Y, int T,
+    const uint8_t *__restrict__ grey, int X, int Y, int T, int fill_mode,
     uint8_t *dl_out, uint8_t *dr_out, uint8_t *gcp_out, uint8_t *dm_out, float *__restrict__ dplus)
 {
     extern __shared__ __align__(16) uint8_t sm[];
@@ -132,7 +132,11 @@ __global__ void __launch_bounds__(kRefNT) refine_kernel(
             if (hl && hr) {
                 const int i = x - li, j = ri - x;
                 const int a = dm[li], b = dm[ri];
-                if (abs(a - b) <= T) {
+                if (fill_mode == 1) {
+                    v = (float)(i < j ? a : b);           // the closer GCP (Fig. 5a)
+                } else if (fill_mode == 2) {
+                    v = (float)min(a, b);                 // the smaller disparity (Fig. 5b)
+                } else if (abs(a - b) <= T) {
                     // linear fill between the two GCPs (Step 7); exact numerator
                     v = __fdiv_rn(__int2float_rn(a * j + b * i), __int2float_rn(i + j));
                 } else {
@@ -217,11 +221,12 @@ cudaError_t refine_setup()
 }
 
 cudaError_t launch_refine(const uint32_t *key_l, const uint32_t *key_r, const uint8_t *grey_l,
-                          int X, int Y, int T, uint8_t *dl, uint8_t *dr, uint8_t *gcp, uint8_t *dm,
-                          float *dplus, cudaStream_t s)
+                          int X, int Y, int T, int fill_mode, uint8_t *dl, uint8_t *dr, uint8_t *gcp,
+                          uint8_t *dm, float *dplus, cudaStream_t s)
 {
-    if (X > kMaxRefineX) return cudaErrorInvalidValue;
-    refine_kernel<<<Y, kRefNT, refine_smem(X), s>>>(key_l, key_r, grey_l, X, Y, T, dl, dr, gcp, dm, dplus);
+    if (X > kMaxRefineX || fill_mode < 0 || fill_mode > 2) return cudaErrorInvalidValue;
+    refine_kernel<<<Y, kRefNT, refine_smem(X), s>>>(key_l, key_r, grey_l, X, Y, T, fill_mode, dl, dr, gcp, dm,
+                                                    dplus);
     return cudaGetLastError();
 }
 

@@ -143,6 +143,7 @@ int check_params(stereo_ctx *c, const stereo_params &p)
     if (p.wy < 0 || p.wy > kMaxWy) return fail(c, STEREO_EINVAL, "wy must be in [0, %d]", kMaxWy);
     if (p.t_fill < 0 || p.t_fill > 255) return fail(c, STEREO_EINVAL, "t_fill must be in [0, 255]");
     if (p.downscale != 0 && p.downscale != 1) return fail(c, STEREO_EINVAL, "downscale must be 0 or 1");
+    if (p.fill_mode < 0 || p.fill_mode > 2) return fail(c, STEREO_EINVAL, "fill_mode must be 0, 1 or 2");
     if (p.cost_scale < 1 || p.cost_scale > (1 << 20)) return fail(c, STEREO_EINVAL, "cost_scale must be in [1, 2^20]");
     // the fused kernel keeps the cost table in 16 bits
     if (p.cost_scale * ((1.0 - std::exp(-1.0 / p.lambda_ad)) + (1.0 - std::exp(-6.0 / p.lambda_mc))) + 1.0 > 65535.0)
@@ -278,7 +279,7 @@ cudaError_t run_stage(stereo_ctx *c, int stage, cudaStream_t s)
     }
     case STEREO_STAGE_REFINE:
         c->launches++;
-        return launch_refine(c->key[0], c->key[1], c->gs[0], c->X, c->Y, c->p.t_fill, c->out_dl, c->out_dr,
+        return launch_refine(c->key[0], c->key[1], c->gs[0], c->X, c->Y, c->p.t_fill, c->p.fill_mode, c->out_dl, c->out_dr,
                              c->out_gcp, c->dm, c->dplus, s);
     case STEREO_STAGE_UPSCALE:
         if (!ds) return cudaSuccess;
@@ -343,6 +344,7 @@ void stereo_default_params(stereo_params *out)
     out->t_fill = 3;
     out->downscale = 1;
     out->cost_scale = 512;
+    out->fill_mode = 0;
 }
 
 int stereo_create(stereo_ctx **out, int device, const stereo_params *p, size_t mem_cap_bytes)
@@ -688,7 +690,7 @@ cudaError_t batch_prep(stereo_ctx *c, const stereo_job &j, const FrameWs &f, cud
 cudaError_t batch_post(stereo_ctx *c, const stereo_job &j, const FrameWs &f, cudaStream_t s, int &launches)
 {
     float *dplus = c->p.downscale ? f.dplus : j.disp_out;
-    cudaError_t e = launch_refine(f.key[0], f.key[1], f.gs[0], f.X, f.Y, c->p.t_fill, j.dl_out, j.dr_out,
+    cudaError_t e = launch_refine(f.key[0], f.key[1], f.gs[0], f.X, f.Y, c->p.t_fill, c->p.fill_mode, j.dl_out, j.dr_out,
                                   j.gcp_out, f.dm, dplus, s);
     launches++;
     if (e == cudaSuccess && c->p.downscale) {

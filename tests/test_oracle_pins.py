@@ -370,6 +370,35 @@ def test_fill_hand_rows(golden_dir):
         assert out[0].tolist() == [float(v) for v in case["out"]], case["work"]
 
 
+def test_fill_variants_hand_rows(golden_dir):
+    g = _load(golden_dir, "fill_variants.json")
+    for case in g["rows"]:
+        gcp = np.array([case["gcp"]], np.uint8)
+        dm = np.array([case["dm"]], np.uint8)
+        gr = np.zeros_like(dm)
+        for mode, name in ((1, "closer"), (2, "smaller")):
+            out = oracle.fill(dm, gcp, gr, 3, mode)
+            assert out[0].tolist() == [float(v) for v in case[name]], (name, case["work"])
+
+
+def test_fill_variants_bound_the_gcps():
+    # every filled value of the prior-art modes is one of the row's GCP values
+    # (or 0 in a row without GCPs), and the smaller-disparity mode never
+    # exceeds the closer-GCP mode between two GCPs
+    rng = np.random.default_rng(4)
+    gcp = (rng.random((20, 40)) < 0.2).astype(np.uint8)
+    dm = rng.integers(0, 60, size=(20, 40)).astype(np.uint8)
+    g = rng.integers(0, 255, size=(20, 40)).astype(np.uint8)
+    closer, smaller = oracle.fill(dm, gcp, g, 3, 1), oracle.fill(dm, gcp, g, 3, 2)
+    for y in range(20):
+        vals = set(dm[y][gcp[y] == 1].astype(float).tolist()) or {0.0}
+        assert set(closer[y].tolist()) <= vals and set(smaller[y].tolist()) <= vals
+        idx = np.flatnonzero(gcp[y])
+        if len(idx) >= 2:
+            inner = slice(idx[0], idx[-1] + 1)
+            assert (smaller[y][inner] <= closer[y][inner]).all()
+
+
 def test_upscale_closed_forms():
     Y, X = 6, 9
     H, W = 2 * Y, 2 * X

@@ -35,7 +35,7 @@ def _params(**kw):
 def _run_gpu(left, right, dmax, p, tile=-1):
     from paper_2212_00488_gb300 import Stereo, _lib
     st = Stereo(0, lambda_ad=p.lambda_ad, lambda_mc=p.lambda_mc, tc=p.tc, wx=p.wx, wy=p.wy,
-                t_fill=p.t_fill, downscale=p.downscale, cost_scale=p.cost_scale)
+                t_fill=p.t_fill, downscale=p.downscale, cost_scale=p.cost_scale, fill_mode=p.fill_mode)
     _lib.stereo_set_tile(st.ctx, tile)
     lt = torch.from_numpy(np.ascontiguousarray(left)).cuda()
     rt = torch.from_numpy(np.ascontiguousarray(right)).cuda()
@@ -137,6 +137,15 @@ def test_parameter_variants(wx, wy, tc, scale):
     s = scenes.make_scene(200, 120, 24, planes=6, seed=3)
     p = _params(downscale=0, wx=wx, wy=wy, tc=tc, cost_scale=scale)
     _compare(_run_gpu(s.left, s.right, 24, p), oracle.pipeline(s.left, s.right, 24, p), f"wx{wx} wy{wy}")
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_fill_variants(mode):
+    # the prior-art fills of Sec. III-E (Fig. 5), downscaled so the scale-up
+    # runs on the filled map too
+    s = scenes.make_scene(400, 300, 60, planes=8, seed=21 + mode)
+    p = _params(fill_mode=mode)
+    _compare(_run_gpu(s.left, s.right, 60, p), oracle.pipeline(s.left, s.right, 60, p), f"fill mode {mode}")
 
 
 def test_max_disparities():
