@@ -332,6 +332,44 @@ def measure_diff(dev, steps=5, warmup=2, seed=6):
             "grad_theta": [float(v) for v in T.grad.cpu()], "steps": steps, "warmup": warmup}
 
 
+def measure_sweep(dev, frames=20, warmup=3):
+    """Timings beyond the headline workload (fused kernel and whole frame):
+    the arm caps of the paper's Table I grid that the kernel supports, the
+    other Middlebury-like shapes of Sec. V, and Dmax at 1436x992."""
+    import torch
+    from paper_2212_00488_gb300 import Stereo, _lib, scenes
+
+    def time_cfg(W, H, Dmax, **params):
+        pool = [scenes.make_scene(W, H, Dmax, planes=PLANES, seed=SEED + 7 * k) for k in range(4)]
+        L = [torch.from_numpy(p.left).to(dev) for p in pool]
+        R = [torch.from_numpy(p.right).to(dev) for p in pool]
+        st = Stereo(dev.index, **params)
+        out = st(L[0], R[0], Dmax)
+        for i in range(warmup):
+            st(L[i % 4], R[i % 4], Dmax, out=out)
+        torch.cuda.synchronize()
+        _lib.stereo_set_profiling(st.ctx, True)
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(frames):
+            st(L[i % 4], R[i % 4], Dmax, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms, _ = _lib.stereo_stage_ms(st.ctx)
+        tile = _lib.stereo_get_tile(st.ctx, W, H, Dmax)
+        st.close()
+        frame_ms = e0.elapsed_time(e1) / frames
+        return {"W": W, "H": H, "Dmax": Dmax, **params, "frame_ms": round(frame_ms, 4),
+                "fps": round(1e3 / frame_ms, 1), "kernel_ms": round(ms[_lib.STAGE_COSTAGG], 4), "tile": tile}
+
+    window = [time_cfg(W_FULL, H_FULL, DMAX, wx=wx, wy=wy) for wx in (5, 9, 21, 29) for wy in (9, 11, 15, 21, 27, 31)]
+    shapes = [time_cfg(W, H, D) for W, H, D in ((1436, 992, 145), (1482, 994, 128), (1444, 960, 380))]
+    dmax = [time_cfg(W_FULL, H_FULL, D) for D in (64, 128, 145, 256, 380, 511)]
+    return {"frames": frames, "warmup": warmup, "window": window, "shapes": shapes, "dmax": dmax,
+            "note": "arm caps per side; the Table I caps 41, 61, 141 exceed the kernel's wx <= 29"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -459,6 +497,8 @@ def run_ours(args):
             line["forms"] = {"batch": measure_batch(dev, stream),
                              "serve": measure_serve(dev, seconds=args.serve_seconds),
                              "diff": measure_diff(dev)}
+        if args.sweep:
+            line["sweep"] = measure_sweep(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
         print(json.dumps(line), flush=True)
@@ -477,6 +517,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched/served/differentiable forms")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served request stream")
     ap.add_argument("--tile", type=int, default=-1, help="force a tile shape of the fused kernel (-1: automatic)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the arm-cap grid, other frame shapes and Dmax (about a minute)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -86,6 +86,15 @@ def test_paper_shape_full_pipeline():
     _compare(_run_gpu(s.left, s.right, 145, p), oracle.pipeline(s.left, s.right, 145, p), "1436x992/145")
 
 
+@pytest.mark.parametrize("W,H,dmax", [(1482, 994, 128), (1444, 960, 380)])
+def test_other_middlebury_like_shapes(W, H, dmax):
+    # the Pipes-like and Vintage-like shapes of Sec. V (D = 64 and 190 after
+    # halving; 741 and 722 processed columns)
+    s = scenes.make_scene(W, H, dmax, planes=40, seed=W)
+    p = _params()
+    _compare(_run_gpu(s.left, s.right, dmax, p), oracle.pipeline(s.left, s.right, dmax, p), f"{W}x{H}/{dmax}")
+
+
 @pytest.mark.parametrize("tile", range(NUM_TILES))
 def test_every_tile_shape(tile):
     # each tile shape of the fused kernel gives the oracle's result, on a frame
