@@ -190,24 +190,26 @@ constexpr int kVX = 32;    // pass V: columns per CTA
 constexpr int kVY = 16;    // pass V: outputs per column tile
 constexpr int kSupNT = 256;
 
-__global__ void __launch_bounds__(kSupNT) support_h_kernel(
-    const uint8_t *__restrict__ g_l, const uint8_t *__restrict__ g_r,
-    uint32_t *__restrict__ pix_l, uint32_t *__restrict__ pix_r,
-    uint32_t *__restrict__ arm_l, uint32_t *__restrict__ arm_r,
-    uint32_t *__restrict__ armc_l, uint32_t *__restrict__ armc_r,
-    uint32_t *__restrict__ key_l, uint32_t *__restrict__ key_r, uint32_t *__restrict__ err,
-    int X, int Y, int wx, int tc)
+struct SupportArgs {
+    const uint8_t *g_l, *g_r;
+    uint32_t *pix_l, *pix_r, *arm_l, *arm_r, *armc_l, *armc_r, *key_l, *key_r, *err;
+    int X, Y, wx, wy, tc;
+    int nhx, nhy, nvx, nvy;                       // tiles of pass H and pass V per image
+};
+
+// Pass H on row tile (bx, by) of image bz.
+__device__ __forceinline__ void support_h(const SupportArgs &A, uint8_t *tile, int bx, int by, int bz)
 {
-    extern __shared__ uint8_t tile[];
-    const uint8_t *g = blockIdx.z ? g_r : g_l;
-    uint32_t *pix = blockIdx.z ? pix_r : pix_l;
-    uint16_t *arm = reinterpret_cast<uint16_t *>(blockIdx.z ? arm_r : arm_l);
-    uint16_t *armc = reinterpret_cast<uint16_t *>(blockIdx.z ? armc_r : armc_l);
-    uint32_t *key = blockIdx.z ? key_r : key_l;
+    const int X = A.X, Y = A.Y, wx = A.wx, tc = A.tc;
+    const uint8_t *g = bz ? A.g_r : A.g_l;
+    uint32_t *pix = bz ? A.pix_r : A.pix_l;
+    uint16_t *arm = reinterpret_cast<uint16_t *>(bz ? A.arm_r : A.arm_l);
+    uint16_t *armc = reinterpret_cast<uint16_t *>(bz ? A.armc_r : A.armc_l);
+    uint32_t *key = bz ? A.key_r : A.key_l;
     const int hx = kMaxWx + kArmChunk - 1;      // >= 2, the census reach
     const int TW = kHX + 2 * hx, TH = kHY + 2;
-    const int x0 = blockIdx.x * kHX, y0 = blockIdx.y * kHY;
-    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *err = 0u;
+    const int x0 = bx * kHX, y0 = by * kHY;
+    if ((bx | by | bz | threadIdx.x) == 0) *A.err = 0u;
 
     for (int ty = 0; ty < TH; ++ty) {
         const uint8_t *row = g + (size_t)min(max(y0 - 1 + ty, 0), Y - 1) * X;
@@ -243,18 +245,16 @@ __global__ void __launch_bounds__(kSupNT) support_h_kernel(
     }
 }
 
-__global__ void __launch_bounds__(kSupNT) support_v_kernel(
-    const uint8_t *__restrict__ g_l, const uint8_t *__restrict__ g_r,
-    uint32_t *__restrict__ arm_l, uint32_t *__restrict__ arm_r,
-    uint32_t *__restrict__ armc_l, uint32_t *__restrict__ armc_r, int X, int Y, int wy, int tc)
+// Pass V on column tile (bx, by) of image bz.
+__device__ __forceinline__ void support_v(const SupportArgs &A, uint8_t *tile, int bx, int by, int bz)
 {
-    extern __shared__ uint8_t tile[];
-    const uint8_t *g = blockIdx.z ? g_r : g_l;
-    uint16_t *arm = reinterpret_cast<uint16_t *>(blockIdx.z ? arm_r : arm_l);
-    uint16_t *armc = reinterpret_cast<uint16_t *>(blockIdx.z ? armc_r : armc_l);
+    const int X = A.X, Y = A.Y, wy = A.wy, tc = A.tc;
+    const uint8_t *g = bz ? A.g_r : A.g_l;
+    uint16_t *arm = reinterpret_cast<uint16_t *>(bz ? A.arm_r : A.arm_l);
+    uint16_t *armc = reinterpret_cast<uint16_t *>(bz ? A.armc_r : A.armc_l);
     const int hy = kMaxWy + kArmChunk - 1;
     const int TH = kVY + 2 * hy;
-    const int x0 = blockIdx.x * kVX, y0 = blockIdx.y * kVY;
+    const int x0 = bx * kVX, y0 = by * kVY;
     const int tx = threadIdx.x % kVX, tq = threadIdx.x / kVX;     // kSupNT / kVX threads per column
     const int x = min(x0 + tx, X - 1);
     for (int ty = tq; ty < TH; ty += kSupNT / kVX)
@@ -272,6 +272,23 @@ __global__ void __launch_bounds__(kSupNT) support_v_kernel(
         arm[2 * ((size_t)y * X + x) + 1] = v;
         // the fused kernel reads the up/down arms of output row y in row y + wy
         armc[2 * ((size_t)(y + wy) * X + x) + 1] = v;
+    }
+}
+
+// Both passes in one launch: the first 2 nhx nhy CTAs run pass H, the rest
+// pass V. The passes read only the grey images and write different halves of
+// the arm words, so they need no order between them.
+__global__ void __launch_bounds__(kSupNT) support_kernel(const __grid_constant__ SupportArgs A)
+{
+    extern __shared__ uint8_t tile[];
+    const int nh = A.nhx * A.nhy;
+    int b = blockIdx.x;
+    if (b < 2 * nh) {
+        support_h(A, tile, b % A.nhx, (b / A.nhx) % A.nhy, b / nh);
+    } else {
+        b -= 2 * nh;
+        const int nv = A.nvx * A.nvy;
+        support_v(A, tile, b % A.nvx, (b / A.nvx) % A.nvy, b / nv);
     }
 }
 
@@ -338,14 +355,11 @@ cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix
 {
     if (wx > kMaxWx || wy > kMaxWy) return cudaErrorInvalidValue;
     const int hx = kMaxWx + kArmChunk - 1, hy = kMaxWy + kArmChunk - 1;
-    dim3 gh((X + kHX - 1) / kHX, (Y + kHY - 1) / kHY, 2);
-    support_h_kernel<<<gh, kSupNT, (size_t)(kHX + 2 * hx) * (kHY + 2), s>>>(
-        g_l, g_r, pix_l, pix_r, arm_l, arm_r, armc_l, armc_r, key_l, key_r, err, X, Y, wx, tc);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    dim3 gv((X + kVX - 1) / kVX, (Y + kVY - 1) / kVY, 2);
-    support_v_kernel<<<gv, kSupNT, (size_t)kVX * (kVY + 2 * hy), s>>>(g_l, g_r, arm_l, arm_r, armc_l, armc_r,
-                                                                       X, Y, wy, tc);
+    SupportArgs A{g_l, g_r, pix_l, pix_r, arm_l, arm_r, armc_l, armc_r, key_l, key_r, err, X, Y, wx, wy, tc,
+                  (X + kHX - 1) / kHX, (Y + kHY - 1) / kHY, (X + kVX - 1) / kVX, (Y + kVY - 1) / kVY};
+    const size_t smem_h = (size_t)(kHX + 2 * hx) * (kHY + 2), smem_v = (size_t)kVX * (kVY + 2 * hy);
+    const int blocks = 2 * (A.nhx * A.nhy + A.nvx * A.nvy);
+    support_kernel<<<blocks, kSupNT, smem_h > smem_v ? smem_h : smem_v, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -248,7 +248,7 @@ cudaError_t run_stage(stereo_ctx *c, int stage, cudaStream_t s)
         return launch_grey(c->in_l, c->in_r, c->gf[0], c->gf[1], c->W, c->H, s);
     }
     case STEREO_STAGE_SUPPORT:
-        c->launches += 2;
+        c->launches++;
         return launch_support(c->gs[0], c->gs[1], c->pix[0], c->pix[1], c->arm[0], c->arm[1], c->armc[0],
                               c->armc[1], c->key[0], c->key[1], c->d_err, c->X, c->Y, c->p.wx, c->p.wy,
                               c->p.tc, s);
@@ -682,7 +682,7 @@ cudaError_t batch_prep(stereo_ctx *c, const stereo_job &j, const FrameWs &f, cud
     if (e == cudaSuccess) {
         e = launch_support(f.gs[0], f.gs[1], f.pix[0], f.pix[1], f.arm[0], f.arm[1], f.armc[0], f.armc[1],
                            f.key[0], f.key[1], c->d_err, f.X, f.Y, c->p.wx, c->p.wy, c->p.tc, s);
-        launches += 2;
+        launches++;
     }
     return e;
 }
