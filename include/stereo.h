@@ -156,10 +156,14 @@ STEREO_API int stereo_debug_planes(stereo_ctx *ctx, uint8_t *grey_l, uint8_t *gr
  * Returns EINVAL when no compute has run or the stage is out of range. */
 STEREO_API int stereo_launch_stage(stereo_ctx *ctx, int stage, void *stream);
 
-/* Turns per-stage timing on (1) or off (0) and clears the accumulated times.
- * When on, every stereo_compute records CUDA events between its stages on its
- * stream; the events of a frame are read back only when their slot in a ring
- * of 64 is reused, so profiling adds no synchronisation between frames. */
+/* Turns per-stage timing on or off and clears the accumulated times.
+ *  on: 0 = off; n >= 1 = every n-th stereo_compute from now on (the first
+ *    one included) records CUDA events between its stages on its stream.
+ *    The events sit between the kernels, so a profiled frame runs a few us
+ *    slower; n > 1 keeps that cost off most frames.
+ * The events of a frame are read back only when their slot in a ring of 64 is
+ * reused, so profiling adds no synchronisation between frames. Returns
+ * EINVAL for on < 0. */
 STEREO_API int stereo_set_profiling(stereo_ctx *ctx, int on);
 
 /* Mean per-stage device times (ms) over every compute profiled since

@@ -168,7 +168,8 @@ def stereo_launch_stage(ctx, stage, stream=0):
 
 
 def stereo_set_profiling(ctx, on):
-    return check(ctx, load().stereo_set_profiling(ctx, 1 if on else 0))
+    """on: False/0 off, True/1 every compute, n > 1 every n-th compute."""
+    return check(ctx, load().stereo_set_profiling(ctx, int(on)))
 
 
 def stereo_stage_ms(ctx, n=NUM_STAGES):

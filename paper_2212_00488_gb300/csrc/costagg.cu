@@ -172,6 +172,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             mbar_init(&empty[s], T::NCTP);          // every consumer thread
         }
     }
+    if (!reuse) pdl_wait();                       // the support words and keys of the previous kernel
     __syncthreads();
 
     if (t >= T::NCTP) {
@@ -423,6 +424,7 @@ template <class T>
 __global__ void __launch_bounds__(T::NT, 1) costagg_wta_kernel(const CostAggArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    pdl_trigger();
     int x0, d0;
     tile_at<T>(a, blockIdx.x, x0, d0);
     costagg_tile<T>(a, x0, d0, smem, false);
@@ -436,6 +438,7 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_batch_kernel(const __grid_co
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_tile;
+    pdl_trigger();
     bool reuse = false;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -521,8 +524,7 @@ cudaError_t launch_batch_one(BatchArgs &b, int nsm, cudaStream_t s)
 template <class T>
 cudaError_t launch_one(const CostAggArgs &a, cudaStream_t s)
 {
-    costagg_wta_kernel<T><<<tiles_of<T>(a), T::NT, T::BYTES, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(costagg_wta_kernel<T>, dim3(tiles_of<T>(a)), dim3(T::NT), T::BYTES, s, a);
 }
 
 template <class T>

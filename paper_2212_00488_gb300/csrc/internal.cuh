@@ -37,6 +37,32 @@ struct CostAggArgs {
     int num_sms;                     // SMs of the device (for the pick)
 };
 
+// Programmatic dependent launch between the kernels of a frame: a kernel
+// launched with launch_dependent may start while the previous kernel on the
+// stream is still running; it calls pdl_wait() before it touches anything
+// that kernel writes (the wait returns once the previous grid has completed
+// and its memory is visible). Every kernel calls pdl_trigger() first, so the
+// next one can be scheduled as soon as all of its CTAs are running.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Number of tile shapes of the fused kernel (ids 0 .. kNumTiles-1).
 constexpr int kNumTiles = 5;
 int costagg_pick(const CostAggArgs &a, int nsm);

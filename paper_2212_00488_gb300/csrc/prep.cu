@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kGDX * kGDY) grey_down_kernel(
     uint8_t *__restrict__ s_l, uint8_t *__restrict__ s_r, int W, int H)
 {
     __shared__ __align__(4) uint8_t reg[kGRH][kGRW];
+    pdl_trigger();
     const bool right = blockIdx.z != 0;
     const uint8_t *rgb = right ? rgb_r : rgb_l;
     uint8_t *s = right ? s_r : s_l;
@@ -281,6 +282,8 @@ __device__ __forceinline__ void support_v(const SupportArgs &A, uint8_t *tile, i
 __global__ void __launch_bounds__(kSupNT) support_kernel(const __grid_constant__ SupportArgs A)
 {
     extern __shared__ uint8_t tile[];
+    pdl_trigger();
+    pdl_wait();                                   // the grey images of the previous kernel
     const int nh = A.nhx * A.nhy;
     int b = blockIdx.x;
     if (b < 2 * nh) {
@@ -359,8 +362,7 @@ cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix
                   (X + kHX - 1) / kHX, (Y + kHY - 1) / kHY, (X + kVX - 1) / kVX, (Y + kVY - 1) / kVY};
     const size_t smem_h = (size_t)(kHX + 2 * hx) * (kHY + 2), smem_v = (size_t)kVX * (kVY + 2 * hy);
     const int blocks = 2 * (A.nhx * A.nhy + A.nvx * A.nvy);
-    support_kernel<<<blocks, kSupNT, smem_h > smem_v ? smem_h : smem_v, s>>>(A);
-    return cudaGetLastError();
+    return launch_dependent(support_kernel, dim3(blocks), dim3(kSupNT), smem_h > smem_v ? smem_h : smem_v, s, A);
 }
 
 cudaError_t launch_unpack_planes(const uint32_t *pix, const uint32_t *arm, uint8_t *grey,

@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(kRefNT) refine_kernel(
     uint8_t *dl_out, uint8_t *dr_out, uint8_t *gcp_out, uint8_t *dm_out, float *__restrict__ dplus)
 {
     extern __shared__ __align__(16) uint8_t sm[];
+    pdl_trigger();
+    pdl_wait();                                        // the keys of the fused kernel
     int *lidx = reinterpret_cast<int *>(sm);           // nearest GCP strictly left, -1 if none
     int *ridx = lidx + X;                              // nearest GCP strictly right, INT_MAX if none
     int *scan_sh = ridx + X;                           // 32 ints
@@ -182,6 +184,8 @@ __global__ void upscale_kernel(const float *__restrict__ dp, const uint8_t *__re
                                const uint8_t *__restrict__ gf, int X, int Y, int W, int H, int T,
                                float *__restrict__ out)
 {
+    pdl_trigger();
+    pdl_wait();                                   // the filled map of the refine kernel
     const int bx = blockIdx.x * blockDim.x + threadIdx.x;
     const int by = blockIdx.y;
     const int xo = 2 * bx, yo = 2 * by;
@@ -225,9 +229,8 @@ cudaError_t launch_refine(const uint32_t *key_l, const uint32_t *key_r, const ui
                           uint8_t *dm, float *dplus, cudaStream_t s)
 {
     if (X > kMaxRefineX || fill_mode < 0 || fill_mode > 2) return cudaErrorInvalidValue;
-    refine_kernel<<<Y, kRefNT, refine_smem(X), s>>>(key_l, key_r, grey_l, X, Y, T, fill_mode, dl, dr, gcp, dm,
-                                                    dplus);
-    return cudaGetLastError();
+    return launch_dependent(refine_kernel, dim3(Y), dim3(kRefNT), refine_smem(X), s, key_l, key_r, grey_l, X, Y, T,
+                            fill_mode, dl, dr, gcp, dm, dplus);
 }
 
 cudaError_t launch_upscale(const float *dplus, const uint8_t *grey_low, const uint8_t *grey_full,
@@ -236,10 +239,10 @@ cudaError_t launch_upscale(const float *dplus, const uint8_t *grey_low, const ui
     dim3 grid(((W + 1) / 2 + 127) / 128, (H + 1) / 2);
     const bool pairs = W % 2 == 0 && (reinterpret_cast<uintptr_t>(out) & 7) == 0;
     if (pairs)
-        upscale_kernel<true><<<grid, 128, 0, s>>>(dplus, grey_low, grey_full, X, Y, W, H, T, out);
-    else
-        upscale_kernel<false><<<grid, 128, 0, s>>>(dplus, grey_low, grey_full, X, Y, W, H, T, out);
-    return cudaGetLastError();
+        return launch_dependent(upscale_kernel<true>, grid, dim3(128), 0, s, dplus, grey_low, grey_full, X, Y, W, H,
+                                T, out);
+    return launch_dependent(upscale_kernel<false>, grid, dim3(128), 0, s, dplus, grey_low, grey_full, X, Y, W, H, T,
+                            out);
 }
 
 }  // namespace stereo

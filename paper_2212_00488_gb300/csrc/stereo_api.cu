@@ -66,6 +66,8 @@ struct stereo_ctx {
     };
     static constexpr int kProfRing = 64;
     bool prof = false;
+    int prof_period = 1;                      // profile every prof_period-th compute
+    long prof_count = 0;
     bool prof_events = false;
     ProfSlot prof_ring[kProfRing];
     int prof_next = 0;
@@ -310,7 +312,7 @@ int run_frame(stereo_ctx *c, cudaStream_t s)
 {
     c->launches = 0;
     stereo_ctx::ProfSlot *sl = nullptr;
-    if (c->prof) {
+    if (c->prof && c->prof_count++ % c->prof_period == 0) {
         sl = &c->prof_ring[c->prof_next];
         c->prof_next = (c->prof_next + 1) % stereo_ctx::kProfRing;
         cudaError_t e = harvest(c, *sl);
@@ -539,7 +541,7 @@ int stereo_launch_stage(stereo_ctx *c, int stage, void *stream)
 
 int stereo_set_profiling(stereo_ctx *c, int on)
 {
-    if (!c) return STEREO_EINVAL;
+    if (!c || on < 0) return STEREO_EINVAL;
     DeviceGuard g(c->device);
     if (on && !c->prof_events) {
         for (auto &sl : c->prof_ring)
@@ -556,7 +558,9 @@ int stereo_set_profiling(stereo_ctx *c, int on)
     for (double &a : c->prof_acc) a = 0.0;
     c->prof_n = 0;
     c->prof_next = 0;
-    c->prof = on != 0;
+    c->prof = on > 0;
+    c->prof_period = on > 0 ? on : 1;
+    c->prof_count = 0;
     return STEREO_OK;
 }
 

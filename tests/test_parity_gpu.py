@@ -214,6 +214,23 @@ def test_stage_relaunch_and_profiling():
     st.close()
 
 
+def test_sampled_profiling():
+    # profiling every 3rd compute: 7 computes record frames 0, 3 and 6
+    from paper_2212_00488_gb300 import Stereo, _lib
+    s = scenes.make_scene(200, 100, 20, planes=4, seed=9)
+    st = Stereo(0)
+    lt = torch.from_numpy(s.left).cuda()
+    rt = torch.from_numpy(s.right).cuda()
+    _lib.stereo_set_profiling(st.ctx, 3)
+    for _ in range(7):
+        st(lt, rt, 20)
+    ms, nframes = _lib.stereo_stage_ms(st.ctx)
+    assert nframes == 3 and ms[_lib.STAGE_COSTAGG] > 0
+    with pytest.raises(_lib.StereoError):
+        _lib.stereo_set_profiling(st.ctx, -1)
+    st.close()
+
+
 def test_argument_errors():
     from paper_2212_00488_gb300 import Stereo, _lib
     st = Stereo(0)
