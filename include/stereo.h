@@ -122,6 +122,18 @@ STEREO_API int stereo_compute_host(stereo_ctx *ctx, const uint8_t *left_rgb, con
                                    int W, int H, int Dmax, float *disp_out, uint8_t *dl_out,
                                    uint8_t *dr_out, uint8_t *gcp_out);
 
+/* stereo_compute_host without the final wait: the copies in, the pipeline and
+ * the copies out are queued on the context's stream and the call returns.
+ * The host buffers must stay valid and untouched until the work is done
+ * (stereo_sync); with pinned host memory the copies run on the copy engines
+ * while the SMs work, so two contexts fed alternately overlap one frame's
+ * copies with the other's compute. Calls on one context run in order on its
+ * stream and reuse one staging area. A bounded-wait timeout is reported by
+ * the next stereo_sync. */
+STEREO_API int stereo_compute_host_async(stereo_ctx *ctx, const uint8_t *left_rgb, const uint8_t *right_rgb,
+                                         int W, int H, int Dmax, float *disp_out, uint8_t *dl_out,
+                                         uint8_t *dr_out, uint8_t *gcp_out);
+
 /* Blocks until all work on the context's own stream has finished, then
  * reports STEREO_ETIMEOUT if a bounded wait inside the fused kernel gave up
  * during the last compute (the kernel then returned early and its maps are

@@ -67,6 +67,7 @@ _SIGNATURES = {
     "stereo_last_error": (ctypes.c_char_p, [_ctxp]),
     "stereo_compute": (_i, [_ctxp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "stereo_compute_host": (_i, [_ctxp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "stereo_compute_host_async": (_i, [_ctxp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "stereo_sync": (_i, [_ctxp]),
     "stereo_debug_planes": (_i, [_ctxp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "stereo_launch_stage": (_i, [_ctxp, _i, _vp]),
@@ -151,6 +152,11 @@ def stereo_compute(ctx, left, right, W, H, dmax, disp, dl=0, dr=0, gcp=0, stream
 def stereo_compute_host(ctx, left, right, W, H, dmax, disp, dl=0, dr=0, gcp=0):
     return check(ctx, load().stereo_compute_host(ctx, left, right, W, H, dmax, disp, dl or None, dr or None,
                                                  gcp or None))
+
+
+def stereo_compute_host_async(ctx, left, right, W, H, dmax, disp, dl=0, dr=0, gcp=0):
+    return check(ctx, load().stereo_compute_host_async(ctx, left, right, W, H, dmax, disp, dl or None, dr or None,
+                                                       gcp or None))
 
 
 def stereo_sync(ctx):

@@ -453,8 +453,8 @@ int stereo_compute(stereo_ctx *c, const uint8_t *left_rgb, const uint8_t *right_
     return run_frame(c, s);
 }
 
-int stereo_compute_host(stereo_ctx *c, const uint8_t *left_rgb, const uint8_t *right_rgb, int W, int H,
-                        int Dmax, float *disp_out, uint8_t *dl_out, uint8_t *dr_out, uint8_t *gcp_out)
+int stereo_compute_host_async(stereo_ctx *c, const uint8_t *left_rgb, const uint8_t *right_rgb, int W, int H,
+                              int Dmax, float *disp_out, uint8_t *dl_out, uint8_t *dr_out, uint8_t *gcp_out)
 {
     if (!c) return STEREO_EINVAL;
     c->err.clear();
@@ -489,7 +489,17 @@ int stereo_compute_host(stereo_ctx *c, const uint8_t *left_rgb, const uint8_t *r
         return cuda_fail(c, e, "device-to-host copy");
     if ((e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(c, e, "device-to-host copy");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    return STEREO_OK;
+}
+
+int stereo_compute_host(stereo_ctx *c, const uint8_t *left_rgb, const uint8_t *right_rgb, int W, int H,
+                        int Dmax, float *disp_out, uint8_t *dl_out, uint8_t *dr_out, uint8_t *gcp_out)
+{
+    const int rc = stereo_compute_host_async(c, left_rgb, right_rgb, W, H, Dmax, disp_out, dl_out, dr_out, gcp_out);
+    if (rc != STEREO_OK) return rc;
+    DeviceGuard g(c->device);
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
     if (*c->h_err) return fail(c, STEREO_ETIMEOUT, "a bounded wait in the fused kernel gave up");
     return STEREO_OK;
 }

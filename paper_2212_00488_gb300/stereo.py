@@ -112,12 +112,18 @@ class Stereo:
                                  stream_handle(s))
         return t
 
-    def compute_host(self, left, right, dmax: int, disp, dl=None, dr=None, gcp=None):
-        """Host-buffer variant (numpy arrays or CPU tensors, ideally pinned)."""
+    def compute_host(self, left, right, dmax: int, disp, dl=None, dr=None, gcp=None, wait: bool = True):
+        """Host-buffer variant (numpy arrays or CPU tensors, ideally pinned).
+        wait=False only queues the copies and the pipeline on the context's
+        stream; the buffers must stay untouched until sync()."""
         def ptr(a):
             if a is None:
                 return 0
             return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
         H, W = int(left.shape[0]), int(left.shape[1])
-        _lib.stereo_compute_host(self.ctx, ptr(left), ptr(right), W, H, dmax, ptr(disp), ptr(dl), ptr(dr),
-                                 ptr(gcp))
+        fn = _lib.stereo_compute_host if wait else _lib.stereo_compute_host_async
+        fn(self.ctx, ptr(left), ptr(right), W, H, dmax, ptr(disp), ptr(dl), ptr(dr), ptr(gcp))
+
+    def sync(self):
+        """Waits for the context's stream; raises on a bounded-wait timeout."""
+        _lib.stereo_sync(self.ctx)

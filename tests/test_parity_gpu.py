@@ -193,6 +193,30 @@ def test_host_entry_point_matches_device_entry_point():
     st.close()
 
 
+def test_async_host_calls_over_two_contexts():
+    # frames queued alternately on two contexts without waiting equal the
+    # device-buffer results frame by frame
+    from paper_2212_00488_gb300 import Stereo
+    frames = [scenes.make_scene(320, 240, 40, planes=6, seed=30 + k) for k in range(4)]
+    ref = Stereo(0)
+    want = []
+    for f in frames:
+        d = ref(torch.from_numpy(f.left).cuda(), torch.from_numpy(f.right).cuda(), 40).disp
+        want.append(d.cpu().numpy())
+    ref.close()
+    a, b = Stereo(0), Stereo(0)
+    outs = [torch.empty((240, 320), dtype=torch.float32).pin_memory() for _ in frames]
+    ins = [(torch.from_numpy(f.left).pin_memory(), torch.from_numpy(f.right).pin_memory()) for f in frames]
+    for k, (l, r) in enumerate(ins):
+        (a, b)[k % 2].compute_host(l, r, 40, outs[k], wait=False)
+    a.sync()
+    b.sync()
+    for k in range(len(frames)):
+        assert np.array_equal(outs[k].numpy(), want[k])
+    a.close()
+    b.close()
+
+
 def test_stage_relaunch_and_profiling():
     from paper_2212_00488_gb300 import Stereo, _lib
     from paper_2212_00488_gb300.stereo import stream_handle
