@@ -59,8 +59,9 @@ struct Theta {
 
 __device__ __forceinline__ Theta load_theta(const float *t) { return Theta{t[0], t[1], t[2], t[3]}; }
 
-// One block per row y and chunk: the cost row of each disparity of the chunk
-// in shared memory, then each pixel's own x window summed directly.
+// One block per row y and chunk: the cost rows of all disparities of the
+// chunk in shared memory ([dc][X]), then each pixel's own x window summed
+// directly, every plane in ascending x.
 __global__ void diff_costx_kernel(const float *__restrict__ gL, const float *__restrict__ gR,
                                   const uint32_t *__restrict__ pixL, const uint32_t *__restrict__ pixR,
                                   const uint32_t *__restrict__ arm, const float *__restrict__ theta, int X, int Y,
@@ -71,35 +72,53 @@ __global__ void diff_costx_kernel(const float *__restrict__ gL, const float *__r
     const Theta th = load_theta(theta);
     const float P = th.wad * (1.f - expf(-1.f / th.lad)) + th.wmc * (1.f - expf(-6.f / th.lmc));
     const size_t r = (size_t)y * X;
-    for (int k = 0; k < dc && d0 + k < D; ++k) {
-        const int d = d0 + k;
-        __syncthreads();
-        for (int x = threadIdx.x; x < X; x += blockDim.x) {
+    const int kn = min(dc, D - d0);
+    for (int x = threadIdx.x; x < X; x += blockDim.x) {
+        const float gl = gL[r + x];
+        const uint32_t pl = pixL[r + x];
+        for (int k = 0; k < kn; ++k) {
+            const int d = d0 + k;
             float c = P;
             if (x >= d) {
-                const float a = fabsf(gL[r + x] - gR[r + x - d]);
-                const int h = __popc((pixL[r + x] ^ pixR[r + x - d]) & 0x3F00u);
+                const float a = fabsf(gl - gR[r + x - d]);
+                const int h = __popc((pl ^ pixR[r + x - d]) & 0x3F00u);
                 c = th.wad * (1.f - expf(-a / th.lad)) + th.wmc * (1.f - expf(-(float)h / th.lmc));
             }
-            crow[x] = c;
+            crow[k * X + x] = c;
         }
-        __syncthreads();
-        for (int x = threadIdx.x; x < X; x += blockDim.x) {
-            const uint32_t am = arm[r + x];
-            const int lo = x - (int)(am & 0xFF), hi = x + (int)((am >> 8) & 0xFF);
-            float s = 0.f;
-            for (int t = lo; t <= hi; ++t) s += crow[t];
-            cax[((size_t)k * Y + y) * X + x] = s;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < X; x += blockDim.x) {
+        const uint32_t am = arm[r + x];
+        const int lo = x - (int)(am & 0xFF), hi = x + (int)((am >> 8) & 0xFF);
+        float s[kDC];
+#pragma unroll
+        for (int k = 0; k < kDC; ++k) s[k] = 0.f;
+        for (int t = lo; t <= hi; ++t) {
+#pragma unroll
+            for (int k = 0; k < kDC; ++k)
+                if (k < kn) s[k] += crow[k * X + t];
         }
+#pragma unroll
+        for (int k = 0; k < kDC; ++k)
+            if (k < kn) cax[((size_t)k * Y + y) * X + x] = s[k];
     }
 }
 
-__device__ __forceinline__ float vsum(const float *__restrict__ plane, const uint32_t am, int x, int y, int X)
+// Vertical sums of Eq. 8 for the chunk's dc planes at once: one pass over the
+// anchor's span [y - up, y + down], each plane summed in ascending y.
+__device__ __forceinline__ void vsum_chunk(const float *__restrict__ cax, const uint32_t am, int x, int y, int X,
+                                           size_t plane, int dc, float (&out)[kDC])
 {
     const int up = (am >> 16) & 0xFF, down = am >> 24;
-    float s = 0.f;
-    for (int t = -up; t <= down; ++t) s += plane[(size_t)(y + t) * X + x];
-    return s;
+#pragma unroll
+    for (int k = 0; k < kDC; ++k) out[k] = 0.f;
+    for (int t = -up; t <= down; ++t) {
+        const float *p = cax + (size_t)(y + t) * X + x;
+#pragma unroll
+        for (int k = 0; k < kDC; ++k)
+            if (k < dc) out[k] += p[k * plane];
+    }
 }
 
 // Forward: aggregated cost along y per pixel and an online softmax over d.
@@ -116,8 +135,12 @@ __global__ void diff_vagg_softmax_kernel(const float *__restrict__ cax, const ui
     const float inv_n = 1.f / ns[i];
     float m = first ? -INFINITY : state[3 * i], s = first ? 0.f : state[3 * i + 1],
           sd = first ? 0.f : state[3 * i + 2];
-    for (int k = 0; k < dc && d0 + k < D; ++k) {
-        const float z = -(vsum(cax + (size_t)k * X * Y, am, x, y, X) * inv_n) * inv_tau;
+    float ca[kDC];
+    vsum_chunk(cax, am, x, y, X, (size_t)X * Y, min(dc, D - d0), ca);
+#pragma unroll
+    for (int k = 0; k < kDC; ++k) {
+        if (k >= dc || d0 + k >= D) break;
+        const float z = -(ca[k] * inv_n) * inv_tau;
         const float d = (float)(d0 + k);
         if (z > m) {
             const float f = expf(m - z);
@@ -154,10 +177,14 @@ __global__ void diff_gca_kernel(const float *__restrict__ cax, const uint32_t *_
     const uint32_t am = arm[i];
     const float inv_n = 1.f / ns[i];
     const float m = stats[2 * i], s = stats[2 * i + 1], e = dhat[i], gi = go[i];
-    for (int k = 0; k < dc; ++k) {
+    float ca[kDC];
+    vsum_chunk(cax, am, x, y, X, (size_t)X * Y, min(dc, D - d0), ca);
+#pragma unroll
+    for (int k = 0; k < kDC; ++k) {
+        if (k >= dc) break;
         float v = 0.f;
         if (d0 + k < D) {
-            const float z = -(vsum(cax + (size_t)k * X * Y, am, x, y, X) * inv_n) * inv_tau;
+            const float z = -(ca[k] * inv_n) * inv_tau;
             const float p = expf(z - m) / s;
             v = gi * p * ((float)(d0 + k) - e) * (-inv_tau) * inv_n;
         }
@@ -174,15 +201,23 @@ __global__ void diff_vT_kernel(const float *__restrict__ g0, const uint32_t *__r
     if (i >= X * Y) return;
     const int yp = i / X, x = i - yp * X;
     const int ya = max(yp - wy, 0), yb = min(yp + wy, Y - 1);
-    for (int k = 0; k < dc; ++k) {
-        const float *plane = g0 + (size_t)k * X * Y;
-        float s = 0.f;
-        for (int y = ya; y <= yb; ++y) {
-            const uint32_t am = arm[(size_t)y * X + x];
-            if (y - (int)((am >> 16) & 0xFF) <= yp && yp <= y + (int)(am >> 24)) s += plane[(size_t)y * X + x];
+    // each anchor's arms are read once for all disparities of the chunk; per
+    // disparity the sum still runs over y in ascending order
+    float s[kDC];
+#pragma unroll
+    for (int k = 0; k < kDC; ++k) s[k] = 0.f;
+    for (int y = ya; y <= yb; ++y) {
+        const size_t j = (size_t)y * X + x;
+        const uint32_t am = arm[j];
+        if (y - (int)((am >> 16) & 0xFF) <= yp && yp <= y + (int)(am >> 24)) {
+#pragma unroll
+            for (int k = 0; k < kDC; ++k)
+                if (k < dc) s[k] += g0[(size_t)k * X * Y + j];
         }
-        g1[(size_t)k * X * Y + i] = s;
     }
+#pragma unroll
+    for (int k = 0; k < kDC; ++k)
+        if (k < dc) g1[(size_t)k * X * Y + i] = s[k];
 }
 
 // Backward 3: adjoint of the horizontal sum, gathered: G2(x', y) collects the
@@ -195,15 +230,21 @@ __global__ void diff_hT_kernel(const float *__restrict__ g1, const uint32_t *__r
     const int y = i / X, xp = i - y * X;
     const int xa = max(xp - wx, 0), xb = min(xp + wx, X - 1);
     const size_t r = (size_t)y * X;
-    for (int k = 0; k < dc; ++k) {
-        const float *plane = g1 + (size_t)k * X * Y;
-        float s = 0.f;
-        for (int x = xa; x <= xb; ++x) {
-            const uint32_t am = arm[r + x];
-            if (x - (int)(am & 0xFF) <= xp && xp <= x + (int)((am >> 8) & 0xFF)) s += plane[r + x];
+    // as in diff_vT_kernel: arms once per pixel, ascending x per disparity
+    float s[kDC];
+#pragma unroll
+    for (int k = 0; k < kDC; ++k) s[k] = 0.f;
+    for (int x = xa; x <= xb; ++x) {
+        const uint32_t am = arm[r + x];
+        if (x - (int)(am & 0xFF) <= xp && xp <= x + (int)((am >> 8) & 0xFF)) {
+#pragma unroll
+            for (int k = 0; k < kDC; ++k)
+                if (k < dc) s[k] += g1[(size_t)k * X * Y + r + x];
         }
-        g2[(size_t)k * X * Y + i] = s;
     }
+#pragma unroll
+    for (int k = 0; k < kDC; ++k)
+        if (k < dc) g2[(size_t)k * X * Y + i] = s[k];
 }
 
 // Backward 4: through the cost. Per pixel: its own gradient as the left pixel
@@ -328,6 +369,10 @@ size_t diff_workspace_bytes(int X, int Y, int wy, int B, int D)
 cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
 {
     const int X = a.W, Y = a.H, n = X * Y;
+    // the cost rows of a chunk take up to kDC * 4096 floats of shared memory
+    const cudaError_t attr = cudaFuncSetAttribute(diff_costx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kDC * 4096 * (int)sizeof(float));
+    if (attr != cudaSuccess) return attr;
     const size_t chunk = (size_t)kDC * n;
     char *w = (char *)a.ws;
     auto take = [&](size_t bytes) {
@@ -368,8 +413,8 @@ cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
         float *dh = a.dhat + (size_t)b * n, *st = a.stats + (size_t)b * n * 2;
         for (int c = 0; c < nchunks; ++c) {
             const int d0 = c * kDC, dc = min(kDC, a.D - d0);
-            diff_costx_kernel<<<Y, kDiffNT, (size_t)X * 4, s>>>(gl, gr, pixl, pixr, arml, a.theta, X, Y, a.D, d0,
-                                                                dc, s0);
+            diff_costx_kernel<<<Y, kDiffNT, (size_t)dc * X * 4, s>>>(gl, gr, pixl, pixr, arml, a.theta, X, Y, a.D,
+                                                                     d0, dc, s0);
             if (!a.backward) {
                 diff_vagg_softmax_kernel<<<nblk, kDiffNT, 0, s>>>(s0, arml, ns, X, Y, a.D, d0, dc, inv_tau, state,
                                                                   c == 0, c == nchunks - 1, dh, st);
