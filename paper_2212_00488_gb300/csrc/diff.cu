@@ -366,13 +366,16 @@ size_t diff_workspace_bytes(int X, int Y, int wy, int B, int D)
     return off;
 }
 
+cudaError_t diff_setup()
+{
+    // the cost rows of a chunk take up to kDC * 4096 floats of shared memory
+    return cudaFuncSetAttribute(diff_costx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kDC * 4096 * (int)sizeof(float));
+}
+
 cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
 {
     const int X = a.W, Y = a.H, n = X * Y;
-    // the cost rows of a chunk take up to kDC * 4096 floats of shared memory
-    const cudaError_t attr = cudaFuncSetAttribute(diff_costx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kDC * 4096 * (int)sizeof(float));
-    if (attr != cudaSuccess) return attr;
     const size_t chunk = (size_t)kDC * n;
     char *w = (char *)a.ws;
     auto take = [&](size_t bytes) {

@@ -98,6 +98,9 @@ struct DiffArgs {
     int wx, wy, tc;
 };
 size_t diff_workspace_bytes(int X, int Y, int wy, int B, int D);
+// Sets the differentiable kernels' attributes on the current device (call
+// before diff_run and outside any stream capture).
+cudaError_t diff_setup();
 cudaError_t diff_run(const DiffArgs &a, cudaStream_t s);
 
 // Launchers (each returns the launch error, cudaSuccess on success).

@@ -79,6 +79,7 @@ struct stereo_ctx {
     void *bws = nullptr;
     size_t bws_size = 0;
     std::map<int, cudaGraphExec_t> bexec;   // one graph per batch size, updated in place
+    cudaGraphExec_t dexec[2] = {nullptr, nullptr};   // differentiable forward / backward graphs
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
     std::map<std::string, int> tune;
     void *dws = nullptr;            // workspace of the differentiable form
@@ -416,6 +417,8 @@ void stereo_destroy(stereo_ctx *c)
         if (c->bws) cudaFree(c->bws);
         if (c->dws) cudaFree(c->dws);
         for (auto &kv : c->bexec) cudaGraphExecDestroy(kv.second);
+        for (cudaGraphExec_t ge : c->dexec)
+            if (ge) cudaGraphExecDestroy(ge);
         for (cudaEvent_t ev : {c->ev_in, c->ev_out, c->ev_t0, c->ev_t1})
             if (ev) cudaEventDestroy(ev);
         if (c->d_lut) cudaFree(c->d_lut);
@@ -976,6 +979,51 @@ int diff_common(stereo_ctx *c, int B, int W, int H, int D, const float *l, const
     return STEREO_OK;
 }
 
+// The differentiable form's ~70 launches per frame, captured on the
+// context's stream as one graph (ordered with the caller's stream through
+// events) and replayed; the graph of the last call of the same direction is
+// updated in place, and instantiated anew when the shapes change.
+cudaError_t diff_graph_run(stereo_ctx *c, const DiffArgs &a, cudaStream_t us)
+{
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    if ((e = diff_setup()) != cudaSuccess) return e;
+    if (us != s) {
+        if ((e = cudaEventRecord(c->ev_in, us)) != cudaSuccess || (e = cudaStreamWaitEvent(s, c->ev_in, 0)) != cudaSuccess)
+            return e;
+    }
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    e = diff_run(a, s);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return e != cudaSuccess ? e : e2;
+    }
+    cudaGraphExec_t &exec = c->dexec[a.backward ? 1 : 0];
+    if (exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+    }
+    if (!exec && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        exec = nullptr;
+        return e;
+    }
+    cudaGraphDestroy(graph);
+    if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return e;
+    if (us != s) {
+        if ((e = cudaEventRecord(c->ev_out, s)) != cudaSuccess || (e = cudaStreamWaitEvent(us, c->ev_out, 0)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -994,7 +1042,7 @@ int stereo_diff_forward(stereo_ctx *c, int B, int W, int H, int D, const float *
     a.dhat = dhat;
     a.stats = stats;
     a.backward = 0;
-    cudaError_t e = diff_run(a, stream ? (cudaStream_t)stream : c->stream);
+    cudaError_t e = diff_graph_run(c, a, stream ? (cudaStream_t)stream : c->stream);
     return e == cudaSuccess ? STEREO_OK : cuda_fail(c, e, "kernel launch");
 }
 
@@ -1018,7 +1066,7 @@ int stereo_diff_backward(stereo_ctx *c, int B, int W, int H, int D, const float 
     a.grad_right = grad_right;
     a.grad_theta = grad_theta;
     a.backward = 1;
-    cudaError_t e = diff_run(a, stream ? (cudaStream_t)stream : c->stream);
+    cudaError_t e = diff_graph_run(c, a, stream ? (cudaStream_t)stream : c->stream);
     return e == cudaSuccess ? STEREO_OK : cuda_fail(c, e, "kernel launch");
 }
 
