@@ -15,8 +15,8 @@
 //    C^R(x, y, d) = C^L(x+d, y, d), and for d in the slab the right windows
 //    land inside [x0-wx, x0+XS+DS-1+wx), next to the left windows.
 //
-// Warp roles (the row buffers between them form a ring of RS slots; rows 2k
-// and 2k+1 share one full and one empty mbarrier):
+// Warp roles (the row buffers between them form a ring of RS slots; rows
+// 4k..4k+3 share one full and one empty mbarrier):
 //  * Producer warp p (NPW of them) fills rows y = p, p + NPW, ...: for each
 //    disparity d = d0 + q of the slab, the exclusive row prefix
 //      S_q[i] = sum_{j<i} C^L(x0 - wx + j, y, d)                  (Eq. 7)
@@ -26,7 +26,7 @@
 //    Prefixes are exact modulo 2^16 or 2^32 (16-bit only when every
 //    horizontal window sum is below 2^16, checked on the host).
 //  * Consumer thread (base, column) holds the slab's DS = 4 disparities and
-//    takes two rows per step:
+//    takes four rows per step:
 //      CA_x = S_q[hi] - S_q[lo] over the pixel's own left/right arms  (Eq. 7)
 //      V(y+1) = V(y) + CA_x  -> ring slot (y+1) mod 64
 //      CA(yo) = V(yo + down + 1) - V(yo - up), yo = y - wy          (Eq. 8)
@@ -112,7 +112,7 @@ struct Tile {
     // S row pitch in elements: the G groups of a consumer warp read rows that
     // start LPX words apart modulo the 32 banks (with one group any pitch does)
     static constexpr int SWP = NE + (G == 1 ? 4 : S16 ? 2 * LPX : LPX);
-    static constexpr int NB = RS / 2;         // row pairs (2k, 2k+1) share a full and an empty barrier
+    static constexpr int NB = RS / 4;         // row quads share a full and an empty barrier
     static constexpr int B_BAR = 2 * NB * 8;
     static constexpr int B_RING = kRing * NCT * DPT * 4;
     static constexpr int B_SX = RS * DS * SWP * (int)sizeof(SType);
@@ -123,7 +123,7 @@ struct Tile {
     static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
     static_assert(NT <= 1024, "");
     static_assert(RS >= NPW, "every producer warp needs a slot of its own");
-    static_assert(RS % 2 == 0, "slots are handed over in row pairs");
+    static_assert(RS % 4 == 0, "slots are handed over in row quads");
     static_assert(BYTES <= 232448, "tile exceeds shared memory");
 };
 
@@ -168,7 +168,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 mbar_inval(&full[s]);
                 mbar_inval(&empty[s]);
             }
-            mbar_init(&full[s], 64);                // the two producing warps of a row pair
+            mbar_init(&full[s], 128);               // the four producing warps of a row quad
             mbar_init(&empty[s], T::NCTP);          // every consumer thread
         }
     }
@@ -250,7 +250,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                     if (lane >= o) incl[q] += u;
                 }
             }
-            if (y >= T::RS && !mbar_wait_warp(&empty[s >> 1], ((y / T::RS) - 1) & 1, limit, a.err)) return;
+            if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ((y / T::RS) - 1) & 1, limit, a.err)) return;
 #pragma unroll
             for (int q = 0; q < T::DS; ++q) {
                 const uint32_t excl = incl[q] - run[q];
@@ -259,8 +259,9 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 for (int k = 0; k < T::KE; ++k) row[1 + lane * T::KE + k] = (SType)(excl + c[q][k]);
                 if (lane == 0) row[0] = 0;
             }
-            mbar_arrive(&full[s >> 1]);
-            if (y + 1 == Y && (y & 1) == 0) mbar_arrive(&full[s >> 1]);   // a last row without a partner
+            mbar_arrive(&full[s >> 2]);
+            if (y + 1 == Y)                               // the quad's rows that do not exist
+                for (int k = y & 3; k < 3; ++k) mbar_arrive(&full[s >> 2]);
         }
         return;
     }
@@ -321,11 +322,11 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         }
         if (active) myring[((y + 1) & (kRing - 1)) * T::NCT] = w;
     };
-    // Two rows per step. While both rows are inputs the step has no branch
-    // but the waits, so the loads and arithmetic of the two rows interleave;
-    // idle threads and rows without an output do the same work and drop it.
-    // Arm words are fetched a step ahead. Slabs that lie wholly below D run
-    // without the per-disparity range test.
+    // Four rows per step, one wait per step. While all four rows are inputs
+    // the step has no branch but the wait, so the loads and arithmetic of
+    // the rows interleave; idle threads and rows without an output do the
+    // same work and drop it. Arm words are fetched a step ahead. Slabs that
+    // lie wholly below D run without the per-disparity range test.
     auto sweep = [&](auto part) {
         constexpr bool kPart = decltype(part)::value;
         // packed WTA key of output row yo over this thread's disparities
@@ -341,47 +342,49 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             }
             return best;
         };
-        uint32_t a0 = __ldg(armc), a1 = __ldg(armc + min(1, rows - 1) * X);
-        for (int y = 0; y < rows; y += 2) {
-            const uint32_t n0 = __ldg(armc + min(y + 2, rows - 1) * X);
-            const uint32_t n1 = __ldg(armc + min(y + 3, rows - 1) * X);
-            const int yo0 = y - wy, yo1 = y + 1 - wy;
-            uint32_t c0[T::DPT], c1[T::DPT], k0, k1;
-            if (y + 1 < Y) {
-                if (!mbar_wait_warp(&full[(y % T::RS) >> 1], (y / T::RS) & 1, limit, a.err)) return;
-                hsum(y, a0, c0);
-                hsum(y + 1, a1, c1);
-                mbar_arrive(&empty[(y % T::RS) >> 1]);
-                // Row yo0 reads V down to slot y - 2wy, which shares its ring
-                // slot with y + 2 when wy = 31, so its key is taken before row
-                // y + 1 is pushed.
-                push(y, c0);
-                k0 = vkey(yo0, a0);
-                push(y + 1, c1);
-                k1 = vkey(yo1, a1);
-            } else {
-                // the last input row (when Y is odd) and the rows that only
-                // output; no V beyond V(Y) is ever read
-                if (y < Y) {
-                    if (!mbar_wait_warp(&full[(y % T::RS) >> 1], (y / T::RS) & 1, limit, a.err)) return;
-                    hsum(y, a0, c0);
-                    mbar_arrive(&empty[(y % T::RS) >> 1]);
-                    push(y, c0);
-                }
-                k0 = vkey(yo0, a0);
-                k1 = vkey(yo1, a1);
-            }
+        constexpr int R = 4;                      // rows per step
+        uint32_t am[R];
 #pragma unroll
-            for (int o = 1; o < T::G; o <<= 1) {
-                k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, o));
-                k1 = min(k1, __shfl_xor_sync(0xffffffffu, k1, o));
+        for (int j = 0; j < R; ++j) am[j] = __ldg(armc + min(j, rows - 1) * X);
+        for (int y = 0; y < rows; y += R) {
+            uint32_t an[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) an[j] = __ldg(armc + min(y + R + j, rows - 1) * X);
+            uint32_t c[R][T::DPT], kk[R];
+            if (y + R - 1 < Y) {
+                if (!mbar_wait_warp(&full[(y % T::RS) >> 2], (y / T::RS) & 1, limit, a.err)) return;
+#pragma unroll
+                for (int j = 0; j < R; ++j) hsum(y + j, am[j], c[j]);
+                mbar_arrive(&empty[(y % T::RS) >> 2]);
+#pragma unroll
+                // output row r - wy reads V down to slot r - 2wy, which shares
+                // its ring slot with r + 2 when wy = 31, so each row's key is
+                // taken before the next row is pushed
+                for (int j = 0; j < R; ++j) {
+                    push(y + j, c[j]);
+                    kk[j] = vkey(y + j - wy, am[j]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const int r = y + j;
+                    if (r < Y) {
+                        if (j == 0 && !mbar_wait_warp(&full[(r % T::RS) >> 2], (r / T::RS) & 1, limit, a.err))
+                            return;
+                        hsum(r, am[j], c[j]);
+                        if (j == R - 1 || r + 1 == Y) mbar_arrive(&empty[(r % T::RS) >> 2]);
+                        push(r, c[j]);
+                    }
+                    kk[j] = vkey(r - wy, am[j]);
+                }
             }
             if (g == 0 && valid) {
-                if (yo0 >= 0) atomicMin(key + yo0 * X, k0);
-                if (yo1 >= 0 && y + 1 < rows) atomicMin(key + yo1 * X, k1);
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (y + j - wy >= 0 && y + j < rows) atomicMin(key + (y + j - wy) * X, kk[j]);
             }
-            a0 = n0;
-            a1 = n1;
+#pragma unroll
+            for (int j = 0; j < R; ++j) am[j] = an[j];
         }
     };
     if (d0 + T::DS <= D)
