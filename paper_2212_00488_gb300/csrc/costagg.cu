@@ -92,6 +92,13 @@ __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, u
     return ok;
 }
 
+// Combined cost table: entry (h, ad) = AD(ad) + MC(h) at h * kLutPitch + ad
+// (16-bit entries; Hamming distances 0..6). A row pitch of 136 words moves
+// the rows of successive h by 8 banks, so lanes with small ad and small h
+// read distinct banks.
+constexpr int kLutRows = 7;
+constexpr int kLutPitch = 272;
+
 template <int XS_, int DS_, int KE_, int RS_, bool S16_, int DPT_, int NPW_>
 struct Tile {
     static constexpr int XS = XS_;            // columns per base
@@ -115,11 +122,15 @@ struct Tile {
     static constexpr int NB = RS / 4;         // row quads share a full and an empty barrier
     static constexpr int B_BAR = 2 * NB * 8;
     static constexpr int B_RING = kRing * NCT * DPT * 4;
+    // 16-bit prefixes: the prefixes of disparities 2j and 2j+1 at one column
+    // share a 32-bit word (pair plane j, SWP words per plane); 32-bit
+    // prefixes: one plane per disparity, SWP words each. Same bytes.
     static constexpr int B_SX = RS * DS * SWP * (int)sizeof(SType);
-    static constexpr int B_LUT = 256 * 8 * 2;
+    static constexpr int B_LUT = kLutRows * kLutPitch * 2;
     static constexpr int BYTES = B_BAR + B_RING + B_SX + B_LUT;
     static_assert(DS % DPT == 0 && 32 % G == 0, "the threads of a column sit in adjacent lanes of one warp");
     static_assert(DPT == 4, "ring entries are 16 bytes");
+    static_assert(!S16 || (DS == 4 && G == 1), "pair planes hold the slab's four disparities");
     static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
     static_assert(NT <= 1024, "");
     static_assert(RS >= NPW, "every producer warp needs a slot of its own");
@@ -152,16 +163,20 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + T::NB;
     Vec *ring = reinterpret_cast<Vec *>(smem + T::B_BAR);                     // [64][NCT]
-    SType *sx = reinterpret_cast<SType *>(smem + T::B_BAR + T::B_RING);       // [RS][DS][SWP]
-    uint16_t *lut = reinterpret_cast<uint16_t *>(smem + T::B_BAR + T::B_RING + T::B_SX);  // [256][8]
+    SType *sx = reinterpret_cast<SType *>(smem + T::B_BAR + T::B_RING);       // [RS][DS][SWP] (32-bit)
+    uint32_t *sxw = reinterpret_cast<uint32_t *>(sx);                           // [RS][2][SWP] (16-bit pairs)
+    uint16_t *lut = reinterpret_cast<uint16_t *>(smem + T::B_BAR + T::B_RING + T::B_SX);  // [7][kLutPitch]
 
     const int t = threadIdx.x, lane = t & 31;
     const int X = a.X, Y = a.Y, D = a.D, wx = a.wx, wy = a.wy;
     const uint32_t limit = a.wait_limit;
 
-    // combined cost table: AD(|grey difference|) + MC(Hamming), index ad * 8 + hamming
+    // combined cost table: AD(|grey difference|) + MC(Hamming)
     if (!reuse)
-        for (int i = t; i < 256 * 8; i += T::NT) lut[i] = (uint16_t)(a.lut_ad[i >> 3] + a.lut_mc[i & 7]);
+        for (int i = t; i < kLutRows * kLutPitch; i += T::NT) {
+            const int h = i / kLutPitch, ad = i - h * kLutPitch;
+            lut[i] = ad < 256 ? (uint16_t)(a.lut_ad[ad] + a.lut_mc[h]) : (uint16_t)0;
+        }
     if (t == 0) {
         for (int s = 0; s < T::NB; ++s) {
             if (reuse) {
@@ -227,7 +242,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                         // match of entry k at disparity d0 + q: qv index k + DS-1 - q
                         const uint32_t qk = qv0[k + T::DS - 1 - q];
                         const uint32_t ad = (uint32_t)abs((int)(pk & 0xFF) - (int)(qk & 0xFF));
-                        uint32_t v = lut[ad * 8 + __popc((pk ^ qk) & 0x3F00u)];
+                        uint32_t v = lut[__popc((pk ^ qk) & 0x3F00u) * kLutPitch + ad];
                         if (kBorder) v = (inimg >> (k * T::DS + q)) & 1u ? v : P;
                         run[q] += v;
                         c[q][k] = run[q];
@@ -251,13 +266,26 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 }
             }
             if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ((y / T::RS) - 1) & 1, limit, a.err)) return;
+            if constexpr (T::S16) {
+                // lanes write words KE apart (KE odd): no bank conflicts
 #pragma unroll
-            for (int q = 0; q < T::DS; ++q) {
-                const uint32_t excl = incl[q] - run[q];
-                SType *row = sx + (s * T::DS + q) * T::SWP;
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t e0 = incl[2 * j] - run[2 * j], e1 = incl[2 * j + 1] - run[2 * j + 1];
+                    uint32_t *row = sxw + (s * 2 + j) * T::SWP;
 #pragma unroll
-                for (int k = 0; k < T::KE; ++k) row[1 + lane * T::KE + k] = (SType)(excl + c[q][k]);
-                if (lane == 0) row[0] = 0;
+                    for (int k = 0; k < T::KE; ++k)
+                        row[1 + lane * T::KE + k] = __byte_perm(e0 + c[2 * j][k], e1 + c[2 * j + 1][k], 0x5410);
+                    if (lane == 0) row[0] = 0;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < T::DS; ++q) {
+                    const uint32_t excl = incl[q] - run[q];
+                    SType *row = sx + (s * T::DS + q) * T::SWP;
+#pragma unroll
+                    for (int k = 0; k < T::KE; ++k) row[1 + lane * T::KE + k] = (SType)(excl + c[q][k]);
+                    if (lane == 0) row[0] = 0;
+                }
             }
             mbar_arrive(&full[s >> 2]);
             if (y + 1 == Y)                               // the quad's rows that do not exist
@@ -301,16 +329,38 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
 #pragma unroll
     for (int k = 0; k < T::DPT; ++k) V[k] = 0;
 
-    // x-window sums of one input row for this thread's disparities
-    auto hsum = [&](int y, uint32_t am, uint32_t (&cax)[T::DPT]) {
-        const SType *r0 = srow0 + (y % T::RS) * (T::DS * T::SWP);
+    // pair plane 0 of slot 0 at this pixel's own column (16-bit prefixes)
+    const uint32_t *wrow0 = sxw + x + wx;
+    // x-window sums of one input row for this thread's disparities. With
+    // 16-bit prefixes a warp of left-base columns (kLeft) reads both
+    // disparities of a pair plane with one 32-bit load; right-base columns
+    // read disparity k at column + k, so each half on its own.
+    auto hsum = [&](auto left, int y, uint32_t am, uint32_t (&cax)[T::DPT]) {
+        constexpr bool kLeft = decltype(left)::value;
         const int hi = ((am >> 8) & 0xFF) + 1, lo = am & 0xFF;
+        if constexpr (T::S16) {
+            const uint32_t *w = wrow0 + (y % T::RS) * (2 * T::SWP);
+            if constexpr (kLeft) {
 #pragma unroll
-        for (int k = 0; k < T::DPT; ++k) {
-            const SType *rk = r0 + k * (T::SWP + (b ? 1 : 0));
-            uint32_t c = (uint32_t)rk[hi] - (uint32_t)rk[-lo];
-            if (T::S16) c &= 0xFFFFu;
-            cax[k] = c;
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t h = w[j * T::SWP + hi], l = w[j * T::SWP - lo];
+                    cax[2 * j] = (h - l) & 0xFFFFu;
+                    cax[2 * j + 1] = (h - (l & 0xFFFF0000u)) >> 16;   // no borrow from the low half
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < T::DPT; ++k) {
+                    const uint16_t *hk = reinterpret_cast<const uint16_t *>(w + (k >> 1) * T::SWP + (b ? k : 0)) + (k & 1);
+                    cax[k] = ((uint32_t)hk[2 * hi] - (uint32_t)hk[-2 * lo]) & 0xFFFFu;
+                }
+            }
+        } else {
+            const SType *r0 = srow0 + (y % T::RS) * (T::DS * T::SWP);
+#pragma unroll
+            for (int k = 0; k < T::DPT; ++k) {
+                const SType *rk = r0 + k * (T::SWP + (b ? 1 : 0));
+                cax[k] = (uint32_t)rk[hi] - (uint32_t)rk[-lo];
+            }
         }
     };
     auto push = [&](int y, const uint32_t (&cax)[T::DPT]) {
@@ -327,7 +377,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     // the rows interleave; idle threads and rows without an output do the
     // same work and drop it. Arm words are fetched a step ahead. Slabs that
     // lie wholly below D run without the per-disparity range test.
-    auto sweep = [&](auto part) {
+    auto sweep = [&](auto part, auto left) {
         constexpr bool kPart = decltype(part)::value;
         // packed WTA key of output row yo over this thread's disparities
         auto vkey = [&](int yo, uint32_t am) -> uint32_t {
@@ -354,7 +404,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             if (y + R - 1 < Y) {
                 if (!mbar_wait_warp(&full[(y % T::RS) >> 2], (y / T::RS) & 1, limit, a.err)) return;
 #pragma unroll
-                for (int j = 0; j < R; ++j) hsum(y + j, am[j], c[j]);
+                for (int j = 0; j < R; ++j) hsum(left, y + j, am[j], c[j]);
                 mbar_arrive(&empty[(y % T::RS) >> 2]);
 #pragma unroll
                 // output row r - wy reads V down to slot r - 2wy, which shares
@@ -371,7 +421,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                     if (r < Y) {
                         if (j == 0 && !mbar_wait_warp(&full[(r % T::RS) >> 2], (r / T::RS) & 1, limit, a.err))
                             return;
-                        hsum(r, am[j], c[j]);
+                        hsum(left, r, am[j], c[j]);
                         if (j == R - 1 || r + 1 == Y) mbar_arrive(&empty[(r % T::RS) >> 2]);
                         push(r, c[j]);
                     }
@@ -387,10 +437,22 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             for (int j = 0; j < R; ++j) am[j] = an[j];
         }
     };
+    // warps whose columns are all of the left base take the paired loads
+    const bool left_warp = __all_sync(0xffffffffu, b == 0);
+    auto run = [&](auto part) {
+        if constexpr (T::S16) {
+            if (left_warp)
+                sweep(part, std::true_type{});
+            else
+                sweep(part, std::false_type{});
+        } else {
+            sweep(part, std::false_type{});
+        }
+    };
     if (d0 + T::DS <= D)
-        sweep(std::false_type{});
+        run(std::false_type{});
     else
-        sweep(std::true_type{});
+        run(std::true_type{});
 }
 
 // Tiles of a frame, slab by slab. Slab s (first disparity d0 = s DS) needs
