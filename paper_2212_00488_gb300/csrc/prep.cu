@@ -151,45 +151,128 @@ __global__ void __launch_bounds__(kGDX * kGDY) grey_down_kernel(
 //  arms to the high half of the arm words.
 // Coordinates of the staged tiles are clamped to the image (border
 // replication, which census reads); the arm scans stop at the real border.
+//
 // Arm length from the staged pixel t (value c) in direction DIR (+1 or -1,
 // element stride S): the number of consecutive pixels k = 1, 2, ... with
-// |I - c| < tc, at most cap. Most arms are short, so the first step tests 4
-// pixels and later steps 8; the loads of a step overlap. The tile holds
-// kArmChunk - 1 pixels beyond each cap.
+// |I - c| < tc, at most cap (Sec. III-C). Pixels are tested in chunks of
+// kArmChunk; the tile holds kArmChunk - 1 pixels beyond each cap. Arm lengths
+// vary a lot between neighbouring pixels, so a warp whose lanes each follow
+// their own arm to its end idles most lanes while the longest arm finishes.
+// Instead every thread tests the first chunk of each of its arms; the arms
+// that go on are appended to a per-CTA queue, and the threads then take
+// queued arms in turn, one chunk per step, each lane moving to its next arm
+// as soon as one ends, so the lanes stay busy until the queue is drained.
 constexpr int kArmChunk = 8;
+constexpr int kSupNT = 256;                   // threads of a support CTA
 
+// Similar pixels at the head of a chunk of N pixels from p (element step
+// DIR * S).
 template <int DIR, int S, int N>
 __device__ __forceinline__ int arm_chunk(const uint8_t *p, int off, unsigned lim)
 {
     uint32_t m = 0;
 #pragma unroll
     for (int j = 0; j < N; ++j) m |= (uint32_t)((unsigned)(p[DIR * j * S] + off) < lim) << j;
-    return __ffs(~m) - 1;                        // similar pixels at the head of the chunk
+    return __ffs(~m) - 1;
 }
 
-template <int DIR, int S>
-__device__ __forceinline__ int arm_run(const uint8_t *t, int c, int tc, int cap)
+// The same with a step known only at run time (queued arms of both
+// directions).
+__device__ __forceinline__ int arm_chunk_dyn(const uint8_t *p, int step, int off, unsigned lim)
 {
-    // |I - c| < tc  <=>  (unsigned)(I - c + tc - 1) < 2 tc - 1
-    const int off = tc - 1 - c;
-    const unsigned lim = tc > 0 ? (unsigned)(2 * tc - 1) : 0u;   // tc = 0: nothing is similar
-    if (cap <= 0) return 0;
-    int run = arm_chunk<DIR, S, 4>(t + DIR * S, off, lim);
-    int n = min(run, cap);
-    if (run < 4) return n;
-    while (n < cap) {
-        run = arm_chunk<DIR, S, kArmChunk>(t + DIR * (n + 1) * S, off, lim);
-        n = min(n + run, cap);
-        if (run < kArmChunk) break;
-    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < kArmChunk; ++j) m |= (uint32_t)((unsigned)(p[j * step] + off) < lim) << j;
+    return __ffs(~m) - 1;
+}
+
+// |I - c| < tc  <=>  (unsigned)(I - c + tc - 1) < 2 tc - 1; tc = 0: nothing
+// is similar.
+__device__ __forceinline__ unsigned arm_lim(int tc)
+{
+    return tc > 0 ? (unsigned)(2 * tc - 1) : 0u;
+}
+
+// Queue entry of an arm that goes on past its first chunk: the pixel's
+// offset in the tile (12 bits), its output slot (10 bits), the direction
+// (1 bit: 0 towards lower coordinates) and the cap (5 bits).
+__device__ __forceinline__ uint32_t arm_entry(int toff, int slot, int dir, int cap)
+{
+    return (uint32_t)toff | ((uint32_t)slot << 12) | ((uint32_t)dir << 22) | ((uint32_t)cap << 23);
+}
+
+// First chunk of an arm; `more` is set when the arm may go on.
+template <int DIR, int S>
+__device__ __forceinline__ int arm_first(const uint8_t *t, int off, unsigned lim, int cap, bool &more)
+{
+    const int run = arm_chunk<DIR, S, kArmChunk>(t + DIR * S, off, lim);
+    const int n = min(run, cap);
+    more = run == kArmChunk && n < cap;
     return n;
 }
 
-constexpr int kHX = 256;   // pass H: outputs per row tile
+// Appends this thread's queued arms (e[j] where bit j of `more` is set).
+template <int N>
+__device__ __forceinline__ void arm_push(uint32_t *q, int *nq, const uint32_t (&e)[N], uint32_t more)
+{
+    if (more == 0u) return;
+    int w = atomicAdd(nq, __popc(more));
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if ((more >> j) & 1u) q[w++] = e[j];
+}
+
+// Drains the queue: each thread takes entries threadIdx.x, + kSupNT, ...,
+// one chunk per step, and writes each arm's length to res[dir][slot].
+__device__ __forceinline__ void arm_drain(const uint8_t *tile, const uint32_t *q, int nq, uint8_t *res,
+                                          int nslot, int S, int tc)
+{
+    const unsigned lim = arm_lim(tc);
+    int i = threadIdx.x;
+    const uint8_t *p = tile;
+    int step = 0, off = 0, cap = 0, n = 0, slot = 0, dir = 0;
+    auto setup = [&](uint32_t e) {
+        p = tile + (e & 0xFFFu);
+        slot = (e >> 12) & 0x3FF;
+        dir = (e >> 22) & 1;
+        cap = (int)(e >> 23);
+        step = dir ? S : -S;
+        off = tc - 1 - (int)p[0];
+        n = kArmChunk;                            // the first chunk was all similar
+    };
+    bool have = i < nq;
+    if (have) setup(q[i]);
+    while (have) {
+        const int run = arm_chunk_dyn(p + step * (n + 1), step, off, lim);
+        n = min(n + run, cap);
+        if (run < kArmChunk || n >= cap) {
+            res[dir * nslot + slot] = (uint8_t)n;
+            i += kSupNT;
+            have = i < nq;
+            if (have) setup(q[i]);
+        }
+    }
+}
+
+constexpr int kHX = 256;   // pass H: outputs per row tile (one column per thread)
 constexpr int kHY = 4;     // pass H: rows per CTA
 constexpr int kVX = 32;    // pass V: columns per CTA
 constexpr int kVY = 16;    // pass V: outputs per column tile
-constexpr int kSupNT = 256;
+constexpr int kHXH = kMaxWx + kArmChunk - 1;   // pass H halo (>= 2, the census reach)
+constexpr int kVYH = kMaxWy + kArmChunk - 1;   // pass V halo
+static_assert(kHX == kSupNT, "pass H: one column per thread");
+static_assert(kSupNT % kVX == 0 && kVY % (kSupNT / kVX) == 0, "pass V: whole rows per thread");
+static_assert((kHX + 2 * kHXH) * (kHY + 2) < 4096 && kVX * (kVY + 2 * kVYH) < 4096, "tile offsets take 12 bits");
+static_assert(kHY * kHX <= 1024 && kVY * kVX <= 1024, "output slots take 10 bits");
+static_assert(kMaxWx < 32 && kMaxWy < 32, "caps take 5 bits");
+
+// Shared memory of one pass: tile, arm lengths [2][slots], queue [2 * slots], count.
+__host__ __device__ constexpr int sup_tile_bytes(int tile, int slots)
+{
+    return (tile + 15) / 16 * 16 + 2 * slots + 4 * 2 * slots + 16;
+}
+constexpr int kSupSmemH = sup_tile_bytes((kHX + 2 * kHXH) * (kHY + 2), kHY * kHX);
+constexpr int kSupSmemV = sup_tile_bytes(kVX * (kVY + 2 * kVYH), kVY * kVX);
 
 struct SupportArgs {
     const uint8_t *g_l, *g_r;
@@ -199,7 +282,7 @@ struct SupportArgs {
 };
 
 // Pass H on row tile (bx, by) of image bz.
-__device__ __forceinline__ void support_h(const SupportArgs &A, uint8_t *tile, int bx, int by, int bz)
+__device__ __forceinline__ void support_h(const SupportArgs &A, uint8_t *smem, int bx, int by, int bz)
 {
     const int X = A.X, Y = A.Y, wx = A.wx, tc = A.tc;
     const uint8_t *g = bz ? A.g_r : A.g_l;
@@ -207,10 +290,14 @@ __device__ __forceinline__ void support_h(const SupportArgs &A, uint8_t *tile, i
     uint16_t *arm = reinterpret_cast<uint16_t *>(bz ? A.arm_r : A.arm_l);
     uint16_t *armc = reinterpret_cast<uint16_t *>(bz ? A.armc_r : A.armc_l);
     uint32_t *key = bz ? A.key_r : A.key_l;
-    const int hx = kMaxWx + kArmChunk - 1;      // >= 2, the census reach
-    const int TW = kHX + 2 * hx, TH = kHY + 2;
+    constexpr int hx = kHXH, TW = kHX + 2 * hx, TH = kHY + 2, NS = kHY * kHX;
+    uint8_t *tile = smem;
+    uint8_t *res = smem + (TW * TH + 15) / 16 * 16;              // [2][NS]
+    uint32_t *q = reinterpret_cast<uint32_t *>(res + 2 * NS);   // [2 NS]
+    int *nq = reinterpret_cast<int *>(q + 2 * NS);
     const int x0 = bx * kHX, y0 = by * kHY;
     if ((bx | by | bz | threadIdx.x) == 0) *A.err = 0u;
+    if (threadIdx.x == 0) *nq = 0;
 
     for (int ty = 0; ty < TH; ++ty) {
         const uint8_t *row = g + (size_t)min(max(y0 - 1 + ty, 0), Y - 1) * X;
@@ -223,56 +310,100 @@ __device__ __forceinline__ void support_h(const SupportArgs &A, uint8_t *tile, i
     // mirror-symmetric in x; bit k set when neighbour k is strictly darker.
     const int cdx[6] = {-1, +1, -2, +2, -1, +1};
     const int cdy[6] = {-1, -1, 0, 0, +1, +1};
+    const unsigned lim = arm_lim(tc);
+    const int ox = threadIdx.x, x = x0 + ox;
+    uint32_t e[2 * kHY], more = 0;
+#pragma unroll
     for (int oy = 0; oy < kHY; ++oy) {
         const int y = y0 + oy;
-        if (y >= Y) break;
-        for (int ox = threadIdx.x; ox < kHX; ox += kSupNT) {
-            const int x = x0 + ox;
-            if (x >= X) break;
-            const uint8_t *t = tile + (oy + 1) * TW + ox + hx;
-            const int c = t[0];
-            uint32_t code = 0;
+        const bool valid = x < X && y < Y;
+        const int toff = (oy + 1) * TW + ox + hx;
+        const uint8_t *t = tile + toff;
+        const int c = t[0];
+        uint32_t code = 0;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) code |= (uint32_t)(t[cdy[k] * TW + cdx[k]] < c) << k;
-            const int hm = arm_run<-1, 1>(t, c, tc, min(wx, x));
-            const int hp = arm_run<1, 1>(t, c, tc, min(wx, X - 1 - x));
+        for (int k = 0; k < 6; ++k) code |= (uint32_t)(t[cdy[k] * TW + cdx[k]] < c) << k;
+        const int off = tc - 1 - c;
+        const int cm = valid ? min(wx, x) : 0, cp = valid ? min(wx, X - 1 - x) : 0;
+        bool mm, mp;
+        const int slot = oy * kHX + ox;
+        res[slot] = (uint8_t)arm_first<-1, 1>(t, off, lim, cm, mm);
+        res[NS + slot] = (uint8_t)arm_first<1, 1>(t, off, lim, cp, mp);
+        e[2 * oy] = arm_entry(toff, slot, 0, cm);
+        e[2 * oy + 1] = arm_entry(toff, slot, 1, cp);
+        more |= ((uint32_t)mm << (2 * oy)) | ((uint32_t)mp << (2 * oy + 1));
+        if (valid) {
             const size_t idx = (size_t)y * X + x;
             pix[idx] = (uint32_t)c | (code << 8);
-            const uint16_t h = (uint16_t)(hm | (hp << 8));
+            key[idx] = 0xFFFFFFFFu;               // WTA key preset: the fused kernel takes atomic minima
+        }
+    }
+    arm_push(q, nq, e, more);
+    __syncthreads();
+    arm_drain(tile, q, *nq, res, NS, 1, tc);
+    __syncthreads();
+#pragma unroll
+    for (int oy = 0; oy < kHY; ++oy) {
+        const int y = y0 + oy, slot = oy * kHX + ox;
+        if (x < X && y < Y) {
+            const size_t idx = (size_t)y * X + x;
+            const uint16_t h = (uint16_t)(res[slot] | (res[NS + slot] << 8));
             arm[2 * idx] = h;
             armc[2 * idx] = h;      // the fused kernel reads row y's left/right arms in row y
-            key[idx] = 0xFFFFFFFFu; // WTA key preset: the fused kernel takes atomic minima
         }
     }
 }
 
 // Pass V on column tile (bx, by) of image bz.
-__device__ __forceinline__ void support_v(const SupportArgs &A, uint8_t *tile, int bx, int by, int bz)
+__device__ __forceinline__ void support_v(const SupportArgs &A, uint8_t *smem, int bx, int by, int bz)
 {
     const int X = A.X, Y = A.Y, wy = A.wy, tc = A.tc;
     const uint8_t *g = bz ? A.g_r : A.g_l;
     uint16_t *arm = reinterpret_cast<uint16_t *>(bz ? A.arm_r : A.arm_l);
     uint16_t *armc = reinterpret_cast<uint16_t *>(bz ? A.armc_r : A.armc_l);
-    const int hy = kMaxWy + kArmChunk - 1;
-    const int TH = kVY + 2 * hy;
+    constexpr int hy = kVYH, TH = kVY + 2 * hy, NS = kVY * kVX, RPT = kVY / (kSupNT / kVX);
+    uint8_t *tile = smem;
+    uint8_t *res = smem + (kVX * TH + 15) / 16 * 16;            // [2][NS]
+    uint32_t *q = reinterpret_cast<uint32_t *>(res + 2 * NS);   // [2 NS]
+    int *nq = reinterpret_cast<int *>(q + 2 * NS);
     const int x0 = bx * kVX, y0 = by * kVY;
     const int tx = threadIdx.x % kVX, tq = threadIdx.x / kVX;     // kSupNT / kVX threads per column
     const int x = min(x0 + tx, X - 1);
+    if (threadIdx.x == 0) *nq = 0;
     for (int ty = tq; ty < TH; ty += kSupNT / kVX)
         tile[ty * kVX + tx] = __ldg(g + (size_t)min(max(y0 - hy + ty, 0), Y - 1) * X + x);
     __syncthreads();
-    if (x0 + tx >= X) return;
-    for (int oy = tq; oy < kVY; oy += kSupNT / kVX) {
-        const int y = y0 + oy;
-        if (y >= Y) break;
-        const uint8_t *t = tile + (oy + hy) * kVX + tx;
-        const int c = t[0];
-        const int vm = arm_run<-1, kVX>(t, c, tc, min(wy, y));
-        const int vp = arm_run<1, kVX>(t, c, tc, min(wy, Y - 1 - y));
-        const uint16_t v = (uint16_t)(vm | (vp << 8));
-        arm[2 * ((size_t)y * X + x) + 1] = v;
-        // the fused kernel reads the up/down arms of output row y in row y + wy
-        armc[2 * ((size_t)(y + wy) * X + x) + 1] = v;
+    const unsigned lim = arm_lim(tc);
+    uint32_t e[2 * RPT], more = 0;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int oy = tq + r * (kSupNT / kVX), y = y0 + oy;
+        const bool valid = x0 + tx < X && y < Y;
+        const int toff = (oy + hy) * kVX + tx;
+        const uint8_t *t = tile + toff;
+        const int off = tc - 1 - (int)t[0];
+        const int cm = valid ? min(wy, y) : 0, cp = valid ? min(wy, Y - 1 - y) : 0;
+        bool mm, mp;
+        const int slot = oy * kVX + tx;
+        res[slot] = (uint8_t)arm_first<-1, kVX>(t, off, lim, cm, mm);
+        res[NS + slot] = (uint8_t)arm_first<1, kVX>(t, off, lim, cp, mp);
+        e[2 * r] = arm_entry(toff, slot, 0, cm);
+        e[2 * r + 1] = arm_entry(toff, slot, 1, cp);
+        more |= ((uint32_t)mm << (2 * r)) | ((uint32_t)mp << (2 * r + 1));
+    }
+    arm_push(q, nq, e, more);
+    __syncthreads();
+    arm_drain(tile, q, *nq, res, NS, kVX, tc);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int oy = tq + r * (kSupNT / kVX), y = y0 + oy, slot = oy * kVX + tx;
+        if (x0 + tx < X && y < Y) {
+            const uint16_t v = (uint16_t)(res[slot] | (res[NS + slot] << 8));
+            arm[2 * ((size_t)y * X + x) + 1] = v;
+            // the fused kernel reads the up/down arms of output row y in row y + wy
+            armc[2 * ((size_t)(y + wy) * X + x) + 1] = v;
+        }
     }
 }
 
@@ -281,17 +412,17 @@ __device__ __forceinline__ void support_v(const SupportArgs &A, uint8_t *tile, i
 // the arm words, so they need no order between them.
 __global__ void __launch_bounds__(kSupNT) support_kernel(const __grid_constant__ SupportArgs A)
 {
-    extern __shared__ uint8_t tile[];
+    extern __shared__ __align__(16) uint8_t smem[];
     pdl_trigger();
     pdl_wait();                                   // the grey images of the previous kernel
     const int nh = A.nhx * A.nhy;
     int b = blockIdx.x;
     if (b < 2 * nh) {
-        support_h(A, tile, b % A.nhx, (b / A.nhx) % A.nhy, b / nh);
+        support_h(A, smem, b % A.nhx, (b / A.nhx) % A.nhy, b / nh);
     } else {
         b -= 2 * nh;
         const int nv = A.nvx * A.nvy;
-        support_v(A, tile, b % A.nvx, (b / A.nvx) % A.nvy, b / nv);
+        support_v(A, smem, b % A.nvx, (b / A.nvx) % A.nvy, b / nv);
     }
 }
 
@@ -357,12 +488,11 @@ cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix
                            int tc, cudaStream_t s)
 {
     if (wx > kMaxWx || wy > kMaxWy) return cudaErrorInvalidValue;
-    const int hx = kMaxWx + kArmChunk - 1, hy = kMaxWy + kArmChunk - 1;
     SupportArgs A{g_l, g_r, pix_l, pix_r, arm_l, arm_r, armc_l, armc_r, key_l, key_r, err, X, Y, wx, wy, tc,
                   (X + kHX - 1) / kHX, (Y + kHY - 1) / kHY, (X + kVX - 1) / kVX, (Y + kVY - 1) / kVY};
-    const size_t smem_h = (size_t)(kHX + 2 * hx) * (kHY + 2), smem_v = (size_t)kVX * (kVY + 2 * hy);
     const int blocks = 2 * (A.nhx * A.nhy + A.nvx * A.nvy);
-    return launch_dependent(support_kernel, dim3(blocks), dim3(kSupNT), smem_h > smem_v ? smem_h : smem_v, s, A);
+    return launch_dependent(support_kernel, dim3(blocks), dim3(kSupNT),
+                            (size_t)(kSupSmemH > kSupSmemV ? kSupSmemH : kSupSmemV), s, A);
 }
 
 cudaError_t launch_unpack_planes(const uint32_t *pix, const uint32_t *arm, uint8_t *grey,

@@ -141,7 +141,9 @@ def test_edge_shapes(W, H, dmax, ds):
 
 
 @pytest.mark.parametrize("wx,wy,tc,scale", [(0, 0, 13, 512), (5, 9, 13, 512), (29, 31, 13, 512),
-                                            (21, 31, 40, 512), (21, 31, 13, 2048), (3, 2, 1, 9)])
+                                            (21, 31, 40, 512), (21, 31, 13, 2048), (3, 2, 1, 9),
+                                            (21, 31, 0, 512),      # no pixel is similar: every arm 0
+                                            (29, 31, 256, 512)])   # every pixel is similar: arms at the caps
 def test_parameter_variants(wx, wy, tc, scale):
     s = scenes.make_scene(200, 120, 24, planes=6, seed=3)
     p = _params(downscale=0, wx=wx, wy=wy, tc=tc, cost_scale=scale)
