@@ -388,16 +388,17 @@ def run_ours(args):
     pool = scenes.scene_pool(W_FULL, H_FULL, DMAX, PLANES, SEED + rank, POOL)
     left = [torch.from_numpy(p.left).to(dev) for p in pool]
     right = [torch.from_numpy(p.right).to(dev) for p in pool]
-    # Two contexts, each on its own stream, take alternate frames, so the small
-    # kernels of one frame fill the SMs the other frame's kernels leave idle.
-    st = Stereo(local)
-    st_b = Stereo(local)
+    # Several contexts, each on its own stream, take frames in turn, so the
+    # small kernels of one frame fill the SMs the other frames' kernels leave
+    # idle.
+    nl = args.lanes
+    ctxs = [Stereo(local) for _ in range(nl)]
     if args.tile >= 0:
-        _lib.stereo_set_tile(st.ctx, args.tile)
-        _lib.stereo_set_tile(st_b.ctx, args.tile)
-    stream = torch.cuda.Stream(dev)
-    stream_b = torch.cuda.Stream(dev)
-    lanes = [(st, stream), (st_b, stream_b)]
+        for c_ in ctxs:
+            _lib.stereo_set_tile(c_.ctx, args.tile)
+    streams = [torch.cuda.Stream(dev) for _ in range(nl)]
+    st, stream = ctxs[0], streams[0]
+    lanes = list(zip(ctxs, streams))
     outs = []
     for ctx_, s_ in lanes:
         with torch.cuda.stream(s_):
@@ -405,9 +406,9 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     def frame(i):
-        ctx_, s_ = lanes[i % 2]
+        ctx_, s_ = lanes[i % nl]
         with torch.cuda.stream(s_):
-            ctx_(left[i % POOL], right[i % POOL], DMAX, out=outs[i % 2])
+            ctx_(left[i % POOL], right[i % POOL], DMAX, out=outs[i % nl])
         return _lib.stereo_last_launch_count(ctx_.ctx)
 
     for i in range(args.warmup):
@@ -428,10 +429,12 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
     e0.record(stream)
-    stream_b.wait_event(e0)
+    for s_ in streams[1:]:
+        s_.wait_event(e0)
     for i in range(args.steps):
         launches += frame(i)
-    stream.wait_stream(stream_b)
+    for s_ in streams[1:]:
+        stream.wait_stream(s_)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -440,11 +443,11 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     stage_ms, nframes = _lib.stereo_stage_ms(st.ctx)
     _lib.stereo_set_profiling(st.ctx, False)
-    # the same stages with one lane only (no frame of the other lane competing
+    # the same stages with one lane only (no frame of another lane competing
     # for SMs), after the timed region
     _lib.stereo_set_profiling(st.ctx, 1)
     for i in range(20):
-        frame(2 * i)
+        frame(nl * i)
     torch.cuda.synchronize()
     stage_alone, _ = _lib.stereo_stage_ms(st.ctx)
     _lib.stereo_set_profiling(st.ctx, False)
@@ -457,7 +460,7 @@ def run_ours(args):
     # e2e through the host-buffer entry point, pinned host memory
     hl = [torch.from_numpy(p.left).pin_memory() for p in pool[:4]]
     hr = [torch.from_numpy(p.right).pin_memory() for p in pool[:4]]
-    hdisp = [torch.empty((H_FULL, W_FULL), dtype=torch.float32).pin_memory() for _ in range(2)]
+    hdisp = [torch.empty((H_FULL, W_FULL), dtype=torch.float32).pin_memory() for _ in range(nl)]
     e2e_steps = max(10, min(args.steps, 100))
     # (1) one synchronous call per frame: copy in, pipeline, copy out, wait
     for i in range(3):
@@ -468,21 +471,20 @@ def run_ours(args):
     for i in range(e2e_steps):
         st.compute_host(hl[i % 4], hr[i % 4], DMAX, hdisp[0])
     sync_fps = replicas.aggregate(float(e2e_steps), time.perf_counter() - t0).throughput
-    # (2) the asynchronous call alternating over two contexts (two streams), so
-    # one frame's host copies overlap the other's compute; every frame still
+    # (2) the asynchronous call taking the contexts (streams) in turn, so one
+    # frame's host copies overlap the others' compute; every frame still
     # copies its pair in and its map out inside the timed region
-    pair = [st, st_b]
-    for i in range(4):
-        pair[i % 2].compute_host(hl[i % 4], hr[i % 4], DMAX, hdisp[i % 2], wait=False)
-    st.sync()
-    st_b.sync()
+    for i in range(2 * nl):
+        ctxs[i % nl].compute_host(hl[i % 4], hr[i % 4], DMAX, hdisp[i % nl], wait=False)
+    for c_ in ctxs:
+        c_.sync()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        pair[i % 2].compute_host(hl[i % 4], hr[i % 4], DMAX, hdisp[i % 2], wait=False)
-    st.sync()
-    st_b.sync()
+        ctxs[i % nl].compute_host(hl[i % 4], hr[i % 4], DMAX, hdisp[i % nl], wait=False)
+    for c_ in ctxs:
+        c_.sync()
     e2e_dt = time.perf_counter() - t0
     e2e_fps = replicas.aggregate(float(e2e_steps), e2e_dt).throughput
 
@@ -516,7 +518,7 @@ def run_ours(args):
                        "scene": "seeded piecewise-planar, 40 planes, texture sigma 20, sensor sigma 2",
                        "l2": f"inputs rotate over {POOL} pairs ({POOL * W_FULL * H_FULL * 6 / 1e6:.0f} MB > L2)",
                        "parallelism": f"replicas x{world}",
-                       "lanes": "2 library contexts on 2 CUDA streams take alternate frames",
+                       "lanes": f"{nl} library contexts on {nl} CUDA streams take frames in turn",
                        "vs_baseline_ref": "paper Table II: 40 fps on a GTX 780 Ti (context, other hardware)"},
             "mde_per_s": fps * W_FULL * H_FULL * DMAX,
             "stage_ms": dict(zip(_lib.STAGE_NAMES, [round(t, 5) for t in stage_ms])),
@@ -534,15 +536,15 @@ def run_ours(args):
                          "ops_per_cell": OPS_PER_CELL, "cells_per_launch": cells,
                          "kernel_ms": stage_ms[_lib.STAGE_COSTAGG], "frames_timed": nframes,
                          "kernel_timer": f"CUDA events around each stage of every {PROFILE_EVERY}th frame of "
-                                         f"lane A in the timed loop, on the stream the kernels run on (the other "
-                                         f"lane's kernels share the SMs meanwhile)",
+                                         f"lane 0 in the timed loop, on the stream the kernels run on (the other "
+                                         f"lanes' kernels share the SMs meanwhile)",
                          "kernel_ms_one_lane": stage_alone[_lib.STAGE_COSTAGG],
                          "frac_one_lane": OPS_PER_CELL * cells / (stage_alone[_lib.STAGE_COSTAGG] / 1e3) / peak_ops,
                          "tile": _lib.stereo_get_tile(st.ctx, W_FULL, H_FULL, DMAX)},
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 2 * W_FULL * H_FULL * 3,
                     "d2h_bytes_per_step": W_FULL * H_FULL * 4, "steps": e2e_steps,
                     "timer": "host wall clock around K stereo_compute_host_async calls from pinned host buffers, "
-                             "alternating over two contexts, then a sync of both",
+                             f"taking the {nl} contexts in turn, then a sync of all",
                     "synchronous_call_value": sync_fps},
             "gpu_launches": launches,
             "clocks": clk,
@@ -556,8 +558,8 @@ def run_ours(args):
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
         print(json.dumps(line), flush=True)
-    st.close()
-    st_b.close()
+    for c_ in ctxs:
+        c_.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -572,11 +574,16 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched/served/differentiable forms")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served request stream")
     ap.add_argument("--tile", type=int, default=-1, help="force a tile shape of the fused kernel (-1: automatic)")
+    ap.add_argument("--lanes", type=int, default=2,
+                    help="library contexts (each on its own stream) that take frames in turn; with more than two "
+                         "the fused kernel's event time in the timed loop includes waiting for the SMs")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the arm-cap grid, other frame shapes and Dmax (about a minute)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.lanes < 1:
+        ap.error("--lanes must be >= 1")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -14,6 +14,22 @@ __device__ __forceinline__ uint32_t luma(uint32_t r, uint32_t g, uint32_t b)
     return (77u * r + 150u * g + 29u * b + 128u) >> 8;
 }
 
+// The weights of luma() as the bytes of one word (r in byte 0).
+constexpr uint32_t kLumaW = 77u | (150u << 8) | (29u << 16);
+
+// luma() of the four pixels in three aligned words (w0 = r0 g0 b0 r1, w1 =
+// g1 b1 r2 g2, w2 = b2 r3 g3 b3), packed one grey byte per pixel: each
+// weighted sum is a four-byte dot product of the pixel's (r, g, b, -) bytes
+// with (77, 150, 29, 0), and its byte 1 is the grey value (sum >> 8).
+__device__ __forceinline__ uint32_t luma4(uint32_t w0, uint32_t w1, uint32_t w2)
+{
+    const uint32_t l0 = __dp4a(w0, kLumaW, 128u);
+    const uint32_t l1 = __dp4a(__funnelshift_r(w0, w1, 24), kLumaW, 128u);
+    const uint32_t l2 = __dp4a(__funnelshift_r(w1, w2, 16), kLumaW, 128u);
+    const uint32_t l3 = __dp4a(w2, kLumaW << 8, 128u);
+    return __byte_perm(__byte_perm(l0, l1, 0x5151), __byte_perm(l2, l3, 0x5151), 0x5410);
+}
+
 // RGB (HWC) -> grey for both images (blockIdx.y selects the image). Each
 // thread converts four consecutive pixels; with a 4-byte aligned source those
 // twelve bytes are three aligned 32-bit loads.
@@ -27,13 +43,7 @@ __global__ void grey_kernel(const uint8_t *__restrict__ rgb_l, const uint8_t *__
     if (p >= n) return;
     if (kAligned && p + 4 <= n) {
         const uint32_t *w = reinterpret_cast<const uint32_t *>(rgb + 3 * p);
-        uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2);
-        // byte order: w0 = r0 g0 b0 r1 | w1 = g1 b1 r2 g2 | w2 = b2 r3 g3 b3
-        uint32_t y0 = luma(w0 & 0xFF, (w0 >> 8) & 0xFF, (w0 >> 16) & 0xFF);
-        uint32_t y1 = luma(w0 >> 24, w1 & 0xFF, (w1 >> 8) & 0xFF);
-        uint32_t y2 = luma((w1 >> 16) & 0xFF, w1 >> 24, w2 & 0xFF);
-        uint32_t y3 = luma((w2 >> 8) & 0xFF, (w2 >> 16) & 0xFF, w2 >> 24);
-        *reinterpret_cast<uint32_t *>(g + p) = y0 | (y1 << 8) | (y2 << 16) | (y3 << 24);
+        *reinterpret_cast<uint32_t *>(g + p) = luma4(__ldg(w), __ldg(w + 1), __ldg(w + 2));
     } else {
         for (long q = p; q < p + 4 && q < n; ++q)
             g[q] = (uint8_t)luma(rgb[3 * q], rgb[3 * q + 1], rgb[3 * q + 2]);
@@ -112,11 +122,7 @@ __global__ void __launch_bounds__(kGDX * kGDY) grey_down_kernel(
         const int fx = fx0 + 4 * gx, fy = fy0 + ry;
         uint32_t q;
         if (inside[k]) {
-            const uint32_t w0 = w[k][0], w1 = w[k][1], w2 = w[k][2];
-            q = luma(w0 & 0xFF, (w0 >> 8) & 0xFF, (w0 >> 16) & 0xFF) |
-                luma(w0 >> 24, w1 & 0xFF, (w1 >> 8) & 0xFF) << 8 |
-                luma((w1 >> 16) & 0xFF, w1 >> 24, w2 & 0xFF) << 16 |
-                luma((w2 >> 8) & 0xFF, (w2 >> 16) & 0xFF, w2 >> 24) << 24;
+            q = luma4(w[k][0], w[k][1], w[k][2]);
         } else {
             // a group across the left or right border: clamped pixel by pixel
             const uint8_t *row = rgb + (size_t)min(max(fy, 0), H - 1) * 3 * W;
@@ -135,11 +141,17 @@ __global__ void __launch_bounds__(kGDX * kGDY) grey_down_kernel(
     const int lx = threadIdx.x % kGDX, ly = threadIdx.x / kGDX;
     const int x = x0 + lx, y = y0 + ly;
     if (x >= X || y >= Y) return;
-    int sum = 0;
+    // the window's three bytes of a row start at byte 2 lx + 3 (1 or 3 mod 4):
+    // byte sums of the two words that hold them, as dot products with 0/1 masks
+    const int b0 = 2 * lx + 3, wa = b0 >> 2;
+    const uint32_t m0 = (b0 & 3) == 1 ? 0x01010100u : 0x01000000u;
+    const uint32_t m1 = (b0 & 3) == 1 ? 0u : 0x00000101u;
+    uint32_t sum = 0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) sum += reg[2 * ly + j][2 * lx + 3 + i];
+    for (int j = 0; j < 3; ++j) {
+        const uint32_t *rw = reinterpret_cast<const uint32_t *>(reg[2 * ly + j]);
+        sum = __dp4a(rw[wa], m0, __dp4a(rw[wa + 1], m1, sum));
+    }
     s[(size_t)y * X + x] = (uint8_t)((sum + 4) / 9);
 }
 

@@ -8,6 +8,7 @@ namespace {
 
 constexpr int kRefNT = 256;
 constexpr int kMaxRefineX = 4096;   // processed width limit of the row kernel
+constexpr int kRefLoads = 4;        // rows up to kRefNT * kRefLoads wide load in one round
 
 __device__ __forceinline__ int med3(int a, int b, int c)
 {
@@ -87,12 +88,39 @@ __global__ void __launch_bounds__(kRefNT) refine_kernel(
     const int y = blockIdx.x;
     const int yu = max(y - 1, 0), yd = min(y + 1, Y - 1);
     const size_t r = (size_t)y * X;
-    for (int x = threadIdx.x; x < X; x += kRefNT) {
-        dlu[x] = (uint8_t)(__ldg(key_l + (size_t)yu * X + x) & 0xFF);
-        dlc[x] = (uint8_t)(__ldg(key_l + r + x) & 0xFF);
-        dld[x] = (uint8_t)(__ldg(key_l + (size_t)yd * X + x) & 0xFF);
-        drc[x] = (uint8_t)(__ldg(key_r + r + x) & 0xFF);
-        gr[x] = __ldg(grey + r + x);
+    if (X <= kRefNT * kRefLoads) {
+        // every load of the thread in flight at once
+        uint32_t ku[kRefLoads], kc[kRefLoads], kd[kRefLoads], kr[kRefLoads], gv[kRefLoads];
+#pragma unroll
+        for (int k = 0; k < kRefLoads; ++k) {
+            const int x = threadIdx.x + k * kRefNT;
+            if (x < X) {
+                ku[k] = __ldg(key_l + (size_t)yu * X + x);
+                kc[k] = __ldg(key_l + r + x);
+                kd[k] = __ldg(key_l + (size_t)yd * X + x);
+                kr[k] = __ldg(key_r + r + x);
+                gv[k] = __ldg(grey + r + x);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRefLoads; ++k) {
+            const int x = threadIdx.x + k * kRefNT;
+            if (x < X) {
+                dlu[x] = (uint8_t)(ku[k] & 0xFF);
+                dlc[x] = (uint8_t)(kc[k] & 0xFF);
+                dld[x] = (uint8_t)(kd[k] & 0xFF);
+                drc[x] = (uint8_t)(kr[k] & 0xFF);
+                gr[x] = (uint8_t)gv[k];
+            }
+        }
+    } else {
+        for (int x = threadIdx.x; x < X; x += kRefNT) {
+            dlu[x] = (uint8_t)(__ldg(key_l + (size_t)yu * X + x) & 0xFF);
+            dlc[x] = (uint8_t)(__ldg(key_l + r + x) & 0xFF);
+            dld[x] = (uint8_t)(__ldg(key_l + (size_t)yd * X + x) & 0xFF);
+            drc[x] = (uint8_t)(__ldg(key_r + r + x) & 0xFF);
+            gr[x] = __ldg(grey + r + x);
+        }
     }
     __syncthreads();
 
@@ -158,27 +186,16 @@ __global__ void __launch_bounds__(kRefNT) refine_kernel(
     }
 }
 
-// Step 8 row pass for low-res row y at output column xo (see upscale_kernel).
-__device__ __forceinline__ float rowpass(const float *__restrict__ dp, const uint8_t *__restrict__ gs,
-                                         const uint8_t *__restrict__ gf, int X, int W, int T, int xo, int y)
-{
-    const int x = xo >> 1;
-    const float *row = dp + (size_t)y * X;
-    if ((xo & 1) == 0 || x + 1 >= X) return __fmul_rn(2.0f, __ldg(row + min(x, X - 1)));
-    const float a = __ldg(row + x), b = __ldg(row + x + 1);
-    if (fabsf(__fsub_rn(a, b)) <= (float)T) return __fadd_rn(a, b);
-    const int gfull = __ldg(gf + (size_t)(2 * y) * W + xo);
-    const int ga = abs((int)__ldg(gs + (size_t)y * X + x) - gfull);
-    const int gb = abs((int)__ldg(gs + (size_t)y * X + x + 1) - gfull);
-    return __fmul_rn(2.0f, ga < gb ? a : b);
-}
-
 // Step 8: bilateral estimation along x, linear along y; full-resolution
-// disparity units (x2). Odd output columns between two low-res pixels whose
-// disparities differ by more than T take the side whose low-res brightness is
-// strictly closer to the full-res pixel's (else the right side). One thread
-// makes the 2x2 outputs (2x..2x+1, 2y..2y+1) of low-res position (x, y), so
-// each row pass is computed once.
+// disparity units (x2). Even output columns 2x take 2 D(x); odd columns
+// 2x + 1 between two low-res pixels take D(x) + D(x+1) when those differ by
+// at most T, else twice the side whose low-res brightness is strictly closer
+// to the full-res pixel's (else the right side). Output rows 2y take low-res
+// row y, rows 2y + 1 the mean of rows y and y + 1 (row y at the last row).
+// One thread makes the 2x4 outputs (2x..2x+1, 4y'..4y'+3) of low-res column
+// x and rows 2y', 2y'+1: it loads everything the three row passes (rows 2y',
+// 2y'+1, 2y'+2) may need, brightness included, in one round, so each output
+// waits for one memory latency.
 template <bool kPairs>
 __global__ void upscale_kernel(const float *__restrict__ dp, const uint8_t *__restrict__ gs,
                                const uint8_t *__restrict__ gf, int X, int Y, int W, int H, int T,
@@ -187,29 +204,61 @@ __global__ void upscale_kernel(const float *__restrict__ dp, const uint8_t *__re
     pdl_trigger();
     pdl_wait();                                   // the filled map of the refine kernel
     const int bx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int by = blockIdx.y;
-    const int xo = 2 * bx, yo = 2 * by;
-    if (xo >= W || yo >= H) return;
-    const int yc = min(by, Y - 1);
-    float e0 = rowpass(dp, gs, gf, X, W, T, xo, yc);
-    float o0 = xo + 1 < W ? rowpass(dp, gs, gf, X, W, T, xo + 1, yc) : 0.f;
-    float e1 = e0, o1 = o0;
-    if (by + 1 < Y) {
-        const float e2 = rowpass(dp, gs, gf, X, W, T, xo, by + 1);
-        const float o2 = xo + 1 < W ? rowpass(dp, gs, gf, X, W, T, xo + 1, by + 1) : 0.f;
-        e1 = __fmul_rn(0.5f, __fadd_rn(e0, e2));
-        o1 = __fmul_rn(0.5f, __fadd_rn(o0, o2));
+    const int by = 2 * blockIdx.y;                // low-res rows by, by + 1
+    const int xo = 2 * bx;
+    if (xo >= W || 2 * by >= H) return;
+    const bool odd = xo + 1 < W;
+    const bool pair = odd && bx + 1 < X;          // odd column between two low-res pixels
+    const int xc = min(bx, X - 1);
+    float a[3], b[3];
+    int gfull[3], ga[3], gb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int yr = min(by + k, Y - 1);
+        const float *row = dp + (size_t)yr * X;
+        a[k] = __ldg(row + xc);
+        b[k] = a[k];
+        gfull[k] = ga[k] = gb[k] = 0;
+        if (pair) {
+            b[k] = __ldg(row + bx + 1);
+            gfull[k] = __ldg(gf + (size_t)(2 * yr) * W + xo + 1);
+            ga[k] = __ldg(gs + (size_t)yr * X + bx);
+            gb[k] = __ldg(gs + (size_t)yr * X + bx + 1);
+        }
     }
-    float *r0 = out + (size_t)yo * W + xo;
-    if (kPairs) {                                   // W even: 8-byte aligned pairs
-        *reinterpret_cast<float2 *>(r0) = make_float2(e0, o0);
-        if (yo + 1 < H) *reinterpret_cast<float2 *>(r0 + W) = make_float2(e1, o1);
-    } else {
-        r0[0] = e0;
-        if (xo + 1 < W) r0[1] = o0;
-        if (yo + 1 < H) {
-            r0[W] = e1;
-            if (xo + 1 < W) r0[W + 1] = o1;
+    // row passes of low-res rows by, by + 1, by + 2 (clamped to the image)
+    float e[3], o[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e[k] = __fmul_rn(2.0f, a[k]);
+        if (!pair)
+            o[k] = e[k];
+        else if (fabsf(__fsub_rn(a[k], b[k])) <= (float)T)
+            o[k] = __fadd_rn(a[k], b[k]);
+        else
+            o[k] = __fmul_rn(2.0f, abs(ga[k] - gfull[k]) < abs(gb[k] - gfull[k]) ? a[k] : b[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int yo = 2 * (by + k);
+        if (yo >= H) break;
+        const float e0 = e[k], o0 = o[k];
+        float e1 = e0, o1 = o0;
+        if (by + k + 1 < Y) {
+            e1 = __fmul_rn(0.5f, __fadd_rn(e0, e[k + 1]));
+            o1 = __fmul_rn(0.5f, __fadd_rn(o0, o[k + 1]));
+        }
+        float *r0 = out + (size_t)yo * W + xo;
+        if (kPairs) {                               // W even: 8-byte aligned pairs
+            *reinterpret_cast<float2 *>(r0) = make_float2(e0, o0);
+            if (yo + 1 < H) *reinterpret_cast<float2 *>(r0 + W) = make_float2(e1, o1);
+        } else {
+            r0[0] = e0;
+            if (odd) r0[1] = o0;
+            if (yo + 1 < H) {
+                r0[W] = e1;
+                if (odd) r0[W + 1] = o1;
+            }
         }
     }
 }
@@ -236,7 +285,7 @@ cudaError_t launch_refine(const uint32_t *key_l, const uint32_t *key_r, const ui
 cudaError_t launch_upscale(const float *dplus, const uint8_t *grey_low, const uint8_t *grey_full,
                            int X, int Y, int W, int H, int T, float *out, cudaStream_t s)
 {
-    dim3 grid(((W + 1) / 2 + 127) / 128, (H + 1) / 2);
+    dim3 grid(((W + 1) / 2 + 127) / 128, ((H + 1) / 2 + 1) / 2);
     const bool pairs = W % 2 == 0 && (reinterpret_cast<uintptr_t>(out) & 7) == 0;
     if (pairs)
         return launch_dependent(upscale_kernel<true>, grid, dim3(128), 0, s, dplus, grey_low, grey_full, X, Y, W, H,

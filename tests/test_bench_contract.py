@@ -32,3 +32,8 @@ def test_reference_arm_json_line():
 def test_too_few_warmup_steps_are_rejected():
     r = _run("--impl", "reference", "--steps", "1", "--warmup", "1")
     assert r.returncode != 0 and "warmup" in r.stderr
+
+
+def test_zero_lanes_are_rejected():
+    r = _run("--steps", "1", "--warmup", "3", "--lanes", "0")
+    assert r.returncode != 0 and "lanes" in r.stderr
