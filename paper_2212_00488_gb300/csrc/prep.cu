@@ -206,11 +206,11 @@ __device__ __forceinline__ unsigned arm_lim(int tc)
 }
 
 // Queue entry of an arm that goes on past its first chunk: the pixel's
-// offset in the tile (12 bits), its output slot (10 bits), the direction
+// offset in the tile (12 bits), its output slot (11 bits), the direction
 // (1 bit: 0 towards lower coordinates) and the cap (5 bits).
 __device__ __forceinline__ uint32_t arm_entry(int toff, int slot, int dir, int cap)
 {
-    return (uint32_t)toff | ((uint32_t)slot << 12) | ((uint32_t)dir << 22) | ((uint32_t)cap << 23);
+    return (uint32_t)toff | ((uint32_t)slot << 12) | ((uint32_t)dir << 23) | ((uint32_t)cap << 24);
 }
 
 // First chunk of an arm; `more` is set when the arm may go on.
@@ -245,9 +245,9 @@ __device__ __forceinline__ void arm_drain(const uint8_t *tile, const uint32_t *q
     int step = 0, off = 0, cap = 0, n = 0, slot = 0, dir = 0;
     auto setup = [&](uint32_t e) {
         p = tile + (e & 0xFFFu);
-        slot = (e >> 12) & 0x3FF;
-        dir = (e >> 22) & 1;
-        cap = (int)(e >> 23);
+        slot = (e >> 12) & 0x7FF;
+        dir = (e >> 23) & 1;
+        cap = (int)(e >> 24);
         step = dir ? S : -S;
         off = tc - 1 - (int)p[0];
         n = kArmChunk;                            // the first chunk was all similar
@@ -275,7 +275,7 @@ constexpr int kVYH = kMaxWy + kArmChunk - 1;   // pass V halo
 static_assert(kHX == kSupNT, "pass H: one column per thread");
 static_assert(kSupNT % kVX == 0 && kVY % (kSupNT / kVX) == 0, "pass V: whole rows per thread");
 static_assert((kHX + 2 * kHXH) * (kHY + 2) < 4096 && kVX * (kVY + 2 * kVYH) < 4096, "tile offsets take 12 bits");
-static_assert(kHY * kHX <= 1024 && kVY * kVX <= 1024, "output slots take 10 bits");
+static_assert(kHY * kHX <= 2048 && kVY * kVX <= 2048, "output slots take 11 bits");
 static_assert(kMaxWx < 32 && kMaxWy < 32, "caps take 5 bits");
 
 // Shared memory of one pass: tile, arm lengths [2][slots], queue [2 * slots], count.
