@@ -549,10 +549,15 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
         }
-        if not args.no_forms:
-            line["forms"] = {"batch": measure_batch(dev, stream),
-                             "serve": measure_serve(dev, seconds=args.serve_seconds),
-                             "diff": measure_diff(dev)}
+        forms = [] if args.no_forms else [f for f in args.forms.split(",") if f]
+        if forms:
+            line["forms"] = {}
+            if "batch" in forms:
+                line["forms"]["batch"] = measure_batch(dev, stream)
+            if "serve" in forms:
+                line["forms"]["serve"] = measure_serve(dev, seconds=args.serve_seconds)
+            if "diff" in forms:
+                line["forms"]["diff"] = measure_diff(dev)
         if args.sweep:
             line["sweep"] = measure_sweep(dev)
         if world == 1 and not args.no_cpu_baseline:
@@ -572,6 +577,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched/served/differentiable forms")
+    ap.add_argument("--forms", default="batch,serve,diff",
+                    help="comma-separated forms to measure after the pipeline (batch, serve, diff)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served request stream")
     ap.add_argument("--tile", type=int, default=-1, help="force a tile shape of the fused kernel (-1: automatic)")
     ap.add_argument("--lanes", type=int, default=2,
@@ -584,6 +591,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.lanes < 1:
         ap.error("--lanes must be >= 1")
+    if any(f not in ("batch", "serve", "diff") for f in args.forms.split(",") if f):
+        ap.error("--forms takes batch, serve and diff")
     if args.impl == "reference":
         run_reference(args)
     else:
