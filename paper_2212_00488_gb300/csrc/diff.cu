@@ -333,14 +333,36 @@ __global__ void diff_finish_kernel(const float *__restrict__ acc_l, const float 
     }
 }
 
-// Sum of all block partials in one fixed order (double accumulation).
-__global__ void diff_theta_reduce_kernel(const float *__restrict__ part, int nparts, float *__restrict__ grad)
+// Sum of all block partials in a fixed order (double accumulation): thread t
+// adds partials t, t + kRedNT, ... in turn, then a fixed pairwise tree adds
+// the threads' sums, so the result does not depend on scheduling.
+constexpr int kRedNT = 1024;
+
+__global__ void __launch_bounds__(kRedNT) diff_theta_reduce_kernel(const float *__restrict__ part, int nparts,
+                                                                   float *__restrict__ grad)
 {
-    const int c = threadIdx.x;
-    if (c >= 4) return;
-    double s = 0.0;
-    for (int k = 0; k < nparts; ++k) s += (double)part[(size_t)k * 4 + c];
-    grad[c] = (float)s;
+    __shared__ double sh[4][kRedNT];
+    const int t = threadIdx.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int k = t; k < nparts; k += kRedNT) {
+        const float4 v = *reinterpret_cast<const float4 *>(part + (size_t)k * 4);
+        s0 += (double)v.x;
+        s1 += (double)v.y;
+        s2 += (double)v.z;
+        s3 += (double)v.w;
+    }
+    sh[0][t] = s0;
+    sh[1][t] = s1;
+    sh[2][t] = s2;
+    sh[3][t] = s3;
+    __syncthreads();
+    for (int o = kRedNT / 2; o > 0; o >>= 1) {
+        if (t < o)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh[c][t] += sh[c][t + o];
+        __syncthreads();
+    }
+    if (t < 4) grad[t] = (float)sh[t][0];
 }
 
 }  // namespace
@@ -438,7 +460,7 @@ cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (a.backward) {
-        diff_theta_reduce_kernel<<<1, 32, 0, s>>>(part, a.B * nchunks * nblk, a.grad_theta);
+        diff_theta_reduce_kernel<<<1, kRedNT, 0, s>>>(part, a.B * nchunks * nblk, a.grad_theta);
         e = cudaGetLastError();
     }
     return e;
