@@ -45,9 +45,10 @@ TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "costagg_wta_kernel_1436x992_d14
 COSTAGG_SRC = os.path.join(ROOT, "paper_2212_00488_gb300", "csrc", "costagg.cu")
 
 
-def _recorded_traffic():
-    """DRAM bytes per launch of the fused kernel from its last ncu capture, or
-    None when the kernel source has changed since the counters were taken."""
+def _recorded_counters():
+    """The fused kernel's last ncu capture (DRAM bytes and shared-memory
+    wavefronts per launch), or {} when the kernel source has changed since the
+    counters were taken."""
     import hashlib
     try:
         with open(TRAFFIC_RECORD) as f:
@@ -55,8 +56,27 @@ def _recorded_traffic():
         with open(COSTAGG_SRC, "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()
     except (OSError, ValueError):
+        return {}
+    return rec if rec.get("source_sha256") == h else {}
+
+
+def _recorded_traffic():
+    """DRAM bytes per launch of the fused kernel, or None (see _recorded_counters)."""
+    return _recorded_counters().get("traffic_bytes_per_launch")
+
+
+def _shared_pipe(kernel_ms, sm_count, sm_mhz):
+    """The fused kernel against its other limit, the shared-memory pipe: the
+    wavefronts one launch issues (ncu) over its one-lane CUDA-event time,
+    against one wavefront per SM and clock."""
+    wf = _recorded_counters().get("shared_wavefronts_per_launch")
+    if not wf or not kernel_ms:
         return None
-    return rec["traffic_bytes_per_launch"] if rec.get("source_sha256") == h else None
+    achieved = wf / (kernel_ms / 1e3)
+    peak = sm_count * sm_mhz * 1e6
+    return {"wavefronts_per_launch": wf, "achieved_per_s": achieved, "peak_per_s": peak,
+            "frac": achieved / peak, "peak_source": f"{sm_count} SMs x 1 wavefront x {sm_mhz:.0f} MHz",
+            "timer": "kernel_ms_one_lane"}
 
 
 def _peaks():
@@ -533,6 +553,7 @@ def run_ours(args):
                                       "lds_tb_per_s": lds_bps / 1e12,
                                       "frac_of_measured_int32": achieved / int_ops,
                                       "source": "stereo_measure_peaks microbenchmarks on this GPU"},
+                         "shared_pipe": _shared_pipe(stage_alone[_lib.STAGE_COSTAGG], sm_count, sm_mhz),
                          "ops_per_cell": OPS_PER_CELL, "cells_per_launch": cells,
                          "kernel_ms": stage_ms[_lib.STAGE_COSTAGG], "frames_timed": nframes,
                          "kernel_timer": f"CUDA events around each stage of every {PROFILE_EVERY}th frame of "
