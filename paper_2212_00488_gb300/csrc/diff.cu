@@ -13,7 +13,9 @@
 //
 // The volume is never stored: forward and backward walk the disparities in
 // chunks of kDC, keeping per chunk the x-aggregated slab and, in backward,
-// the slab's gradients. Sums over arms are direct (at most 2 wx + 1 and
+// the slab's gradients. Every pair of the batch has its own buffers, and the
+// per-chunk kernels take all pairs in one launch (blockIdx.y = pair), so a
+// launch is several waves of blocks rather than one and a partial one. Sums over arms are direct (at most 2 wx + 1 and
 // 2 wy + 1 terms), which keeps FP32 aggregates within about 6e-6 of their
 // exact value. The adjoint gathers for every cell the anchors whose support
 // contains it, so no float atomics are used and results are deterministic.
@@ -30,6 +32,11 @@ __global__ void diff_grey_kernel(const float *__restrict__ rgb_l, const float *_
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const size_t b = blockIdx.z;                  // pair
+    rgb_l += b * n * 3;
+    rgb_r += b * n * 3;
+    g_l += b * n;
+    g_r += b * n;
     const float *rgb = blockIdx.y ? rgb_r : rgb_l;
     float g = __fmul_rn(kGreyW[0], rgb[3 * i]);
     g = __fadd_rn(g, __fmul_rn(kGreyW[1], rgb[3 * i + 1]));
@@ -42,6 +49,9 @@ __global__ void diff_nsupport_kernel(const uint32_t *__restrict__ arm, int X, in
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= X * Y) return;
+    const size_t b = blockIdx.y;                  // pair
+    arm += b * X * Y;
+    ns += b * X * Y;
     const int y = i / X, x = i - y * X;
     const uint32_t a = arm[i];
     const int up = (a >> 16) & 0xFF, down = a >> 24;
@@ -69,6 +79,13 @@ __global__ void diff_costx_kernel(const float *__restrict__ gL, const float *__r
 {
     extern __shared__ float crow[];
     const int y = blockIdx.x;
+    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    gL += b * n;
+    gR += b * n;
+    pixL += b * n;
+    pixR += b * n;
+    arm += b * n;
+    cax += b * kDC * n;
     const Theta th = load_theta(theta);
     const float P = th.wad * (1.f - expf(-1.f / th.lad)) + th.wmc * (1.f - expf(-6.f / th.lmc));
     const size_t r = (size_t)y * X;
@@ -130,6 +147,13 @@ __global__ void diff_vagg_softmax_kernel(const float *__restrict__ cax, const ui
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= X * Y) return;
+    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    cax += b * kDC * n;
+    arm += b * n;
+    ns += b * n;
+    state += b * 3 * n;
+    dhat += b * n;
+    stats += b * 2 * n;
     const int y = i / X, x = i - y * X;
     const uint32_t am = arm[i];
     const float inv_n = 1.f / ns[i];
@@ -173,6 +197,14 @@ __global__ void diff_gca_kernel(const float *__restrict__ cax, const uint32_t *_
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= X * Y) return;
+    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    cax += b * kDC * n;
+    arm += b * n;
+    ns += b * n;
+    dhat += b * n;
+    stats += b * 2 * n;
+    go += b * n;
+    g0 += b * kDC * n;
     const int y = i / X, x = i - y * X;
     const uint32_t am = arm[i];
     const float inv_n = 1.f / ns[i];
@@ -199,6 +231,10 @@ __global__ void diff_vT_kernel(const float *__restrict__ g0, const uint32_t *__r
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= X * Y) return;
+    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    g0 += b * kDC * n;
+    arm += b * n;
+    g1 += b * kDC * n;
     const int yp = i / X, x = i - yp * X;
     const int ya = max(yp - wy, 0), yb = min(yp + wy, Y - 1);
     // each anchor's arms are read once for all disparities of the chunk; per
@@ -227,6 +263,10 @@ __global__ void diff_hT_kernel(const float *__restrict__ g1, const uint32_t *__r
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= X * Y) return;
+    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    g1 += b * kDC * n;
+    arm += b * n;
+    g2 += b * kDC * n;
     const int y = i / X, xp = i - y * X;
     const int xa = max(xp - wx, 0), xb = min(xp + wx, X - 1);
     const size_t r = (size_t)y * X;
@@ -255,9 +295,18 @@ __global__ void diff_costgrad_kernel(const float *__restrict__ gL, const float *
                                      const uint32_t *__restrict__ pixL, const uint32_t *__restrict__ pixR,
                                      const float *__restrict__ theta, int X, int Y, int D, int d0, int dc,
                                      const float *__restrict__ g2, float *__restrict__ acc_l,
-                                     float *__restrict__ acc_r, float *__restrict__ part)
+                                     float *__restrict__ acc_r, float *__restrict__ part, size_t part_pair)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    gL += b * n;
+    gR += b * n;
+    pixL += b * n;
+    pixR += b * n;
+    g2 += b * kDC * n;
+    acc_l += b * n;
+    acc_r += b * n;
+    part += b * part_pair;
     const Theta th = load_theta(theta);
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
     if (i < X * Y) {
@@ -326,6 +375,11 @@ __global__ void diff_finish_kernel(const float *__restrict__ acc_l, const float 
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const size_t b = blockIdx.y;                  // pair
+    acc_l += b * n;
+    acc_r += b * n;
+    grad_l += b * n * 3;
+    grad_r += b * n * 3;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         grad_l[3 * i + c] = acc_l[i] * kGreyW[c];
@@ -369,23 +423,56 @@ __global__ void __launch_bounds__(kRedNT) diff_theta_reduce_kernel(const float *
 
 constexpr int kDiffNT = 256;
 
-size_t diff_workspace_bytes(int X, int Y, int wy, int B, int D)
+// Workspace of a batch: per-pair planes [B][...] of each kind, then the
+// parameter-gradient partials [B][chunk][block][4]. With base == nullptr
+// only the size is computed.
+struct DiffWs {
+    float *gl, *gr;
+    uint8_t *ql, *qr;
+    uint32_t *pixl, *pixr, *arml, *armr, *armcl, *armcr, *keyl, *keyr;
+    float *ns, *state, *accl, *accr, *s0, *s1, *s2, *s3, *part;
+};
+
+size_t diff_layout(char *base, int X, int Y, int wy, int B, int D, DiffWs *w)
 {
-    const size_t n = (size_t)X * Y;
-    const size_t chunk = (size_t)kDC * n * 4;
+    const size_t n = (size_t)X * Y, nb = (size_t)B;
     const size_t nblk = (n + kDiffNT - 1) / kDiffNT;
     const size_t nchunks = (D + kDC - 1) / kDC;
     size_t off = 0;
-    auto take = [&](size_t bytes) { off += (bytes + 255) & ~(size_t)255; };
-    take(n * 4); take(n * 4);                              // float grey
-    take(n); take(n);                                      // integer grey of the uint8 images
-    take(n * 4); take(n * 4); take(n * 4); take(n * 4);    // pixel and arm words
-    take((size_t)X * (Y + wy) * 4); take((size_t)X * (Y + wy) * 4);
-    take(n * 4); take(n * 4);                              // keys (written by the support pass)
-    take(n * 4); take(n * 4 * 3); take(n * 4); take(n * 4); // support size, softmax state, accumulators
-    take(chunk); take(chunk); take(chunk); take(chunk);   // slabs
-    take((size_t)B * nchunks * nblk * 16);                 // parameter-gradient partials
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    DiffWs t;
+    t.gl = (float *)take(nb * n * 4);                        // float grey
+    t.gr = (float *)take(nb * n * 4);
+    t.ql = (uint8_t *)take(nb * n);                          // integer grey of the uint8 images
+    t.qr = (uint8_t *)take(nb * n);
+    t.pixl = (uint32_t *)take(nb * n * 4);                   // pixel and arm words
+    t.pixr = (uint32_t *)take(nb * n * 4);
+    t.arml = (uint32_t *)take(nb * n * 4);
+    t.armr = (uint32_t *)take(nb * n * 4);
+    t.armcl = (uint32_t *)take(nb * X * (size_t)(Y + wy) * 4);
+    t.armcr = (uint32_t *)take(nb * X * (size_t)(Y + wy) * 4);
+    t.keyl = (uint32_t *)take(nb * n * 4);                   // keys (written by the support pass)
+    t.keyr = (uint32_t *)take(nb * n * 4);
+    t.ns = (float *)take(nb * n * 4);                        // support size
+    t.state = (float *)take(nb * n * 4 * 3);                 // online softmax state
+    t.accl = (float *)take(nb * n * 4);                      // intensity-gradient accumulators
+    t.accr = (float *)take(nb * n * 4);
+    t.s0 = (float *)take(nb * kDC * n * 4);                  // slabs
+    t.s1 = (float *)take(nb * kDC * n * 4);
+    t.s2 = (float *)take(nb * kDC * n * 4);
+    t.s3 = (float *)take(nb * kDC * n * 4);
+    t.part = (float *)take(nb * nchunks * nblk * 16);        // parameter-gradient partials
+    if (w) *w = t;
     return off;
+}
+
+size_t diff_workspace_bytes(int X, int Y, int wy, int B, int D)
+{
+    return diff_layout(nullptr, X, Y, wy, B, D, nullptr);
 }
 
 cudaError_t diff_setup()
@@ -397,73 +484,55 @@ cudaError_t diff_setup()
 
 cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
 {
-    const int X = a.W, Y = a.H, n = X * Y;
-    const size_t chunk = (size_t)kDC * n;
-    char *w = (char *)a.ws;
-    auto take = [&](size_t bytes) {
-        char *p = w;
-        w += (bytes + 255) & ~(size_t)255;
-        return p;
-    };
-    float *gl = (float *)take(n * 4), *gr = (float *)take(n * 4);
-    uint8_t *ql = (uint8_t *)take(n), *qr = (uint8_t *)take(n);
-    uint32_t *pixl = (uint32_t *)take(n * 4), *pixr = (uint32_t *)take(n * 4);
-    uint32_t *arml = (uint32_t *)take(n * 4), *armr = (uint32_t *)take(n * 4);
-    uint32_t *armcl = (uint32_t *)take((size_t)X * (Y + a.wy) * 4);
-    uint32_t *armcr = (uint32_t *)take((size_t)X * (Y + a.wy) * 4);
-    uint32_t *keyl = (uint32_t *)take(n * 4), *keyr = (uint32_t *)take(n * 4);
-    float *ns = (float *)take(n * 4), *state = (float *)take(n * 4 * 3);
-    float *accl = (float *)take(n * 4), *accr = (float *)take(n * 4);
-    float *s0 = (float *)take(chunk * 4), *s1 = (float *)take(chunk * 4), *s2 = (float *)take(chunk * 4);
-    float *s3 = (float *)take(chunk * 4);
-    float *part = (float *)w;
+    const int X = a.W, Y = a.H, n = X * Y, B = a.B;
+    DiffWs w;
+    diff_layout((char *)a.ws, X, Y, a.wy, B, a.D, &w);
     const int nblk = (n + kDiffNT - 1) / kDiffNT;
     const int nchunks = (a.D + kDC - 1) / kDC;
+    const size_t part_pair = (size_t)nchunks * nblk * 4;
+    const size_t armc_n = (size_t)X * (Y + a.wy);
     const float inv_tau = 1.f / a.tau;
     cudaError_t e = cudaSuccess;
-    for (int b = 0; b < a.B; ++b) {
-        const float *L = a.left + (size_t)b * n * 3, *R = a.right + (size_t)b * n * 3;
-        diff_grey_kernel<<<dim3(nblk, 2), kDiffNT, 0, s>>>(L, R, gl, gr, n);
-        if ((e = launch_grey(a.left_u8 + (size_t)b * n * 3, a.right_u8 + (size_t)b * n * 3, ql, qr, X, Y, s)) !=
-                cudaSuccess ||
-            (e = launch_support(ql, qr, pixl, pixr, arml, armr, armcl, armcr, keyl, keyr, a.err, X, Y, a.wx, a.wy,
-                                a.tc, s)) != cudaSuccess)
+    // frozen supports of every pair (integer path), support sizes, float grey
+    diff_grey_kernel<<<dim3(nblk, 2, B), kDiffNT, 0, s>>>(a.left, a.right, w.gl, w.gr, n);
+    for (int b = 0; b < B; ++b) {
+        const size_t o = (size_t)b * n;
+        if ((e = launch_grey(a.left_u8 + o * 3, a.right_u8 + o * 3, w.ql + o, w.qr + o, X, Y, s)) != cudaSuccess ||
+            (e = launch_support(w.ql + o, w.qr + o, w.pixl + o, w.pixr + o, w.arml + o, w.armr + o,
+                                w.armcl + b * armc_n, w.armcr + b * armc_n, w.keyl + o, w.keyr + o, a.err, X, Y,
+                                a.wx, a.wy, a.tc, s)) != cudaSuccess)
             return e;
-        diff_nsupport_kernel<<<nblk, kDiffNT, 0, s>>>(arml, X, Y, ns);
-        if (a.backward) {
-            if ((e = cudaMemsetAsync(accl, 0, (size_t)n * 4, s)) != cudaSuccess ||
-                (e = cudaMemsetAsync(accr, 0, (size_t)n * 4, s)) != cudaSuccess)
-                return e;
+    }
+    diff_nsupport_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.arml, X, Y, w.ns);
+    if (a.backward) {
+        if ((e = cudaMemsetAsync(w.accl, 0, (size_t)B * n * 4, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(w.accr, 0, (size_t)B * n * 4, s)) != cudaSuccess)
+            return e;
+    }
+    for (int c = 0; c < nchunks; ++c) {
+        const int d0 = c * kDC, dc = min(kDC, a.D - d0);
+        diff_costx_kernel<<<dim3(Y, B), kDiffNT, (size_t)dc * X * 4, s>>>(w.gl, w.gr, w.pixl, w.pixr, w.arml,
+                                                                          a.theta, X, Y, a.D, d0, dc, w.s0);
+        if (!a.backward) {
+            diff_vagg_softmax_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s0, w.arml, w.ns, X, Y, a.D, d0, dc,
+                                                                       inv_tau, w.state, c == 0, c == nchunks - 1,
+                                                                       a.dhat, a.stats);
+        } else {
+            diff_gca_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s0, w.arml, w.ns, X, Y, a.D, d0, dc, inv_tau,
+                                                              a.dhat, a.stats, a.grad_dhat, w.s1);
+            diff_vT_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s1, w.arml, X, Y, a.wy, dc, w.s2);
+            diff_hT_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s2, w.arml, X, Y, a.wx, dc, w.s3);
+            diff_costgrad_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.gl, w.gr, w.pixl, w.pixr, a.theta, X, Y, a.D,
+                                                                   d0, dc, w.s3, w.accl, w.accr,
+                                                                   w.part + (size_t)c * nblk * 4, part_pair);
         }
-        float *dh = a.dhat + (size_t)b * n, *st = a.stats + (size_t)b * n * 2;
-        for (int c = 0; c < nchunks; ++c) {
-            const int d0 = c * kDC, dc = min(kDC, a.D - d0);
-            diff_costx_kernel<<<Y, kDiffNT, (size_t)dc * X * 4, s>>>(gl, gr, pixl, pixr, arml, a.theta, X, Y, a.D,
-                                                                     d0, dc, s0);
-            if (!a.backward) {
-                diff_vagg_softmax_kernel<<<nblk, kDiffNT, 0, s>>>(s0, arml, ns, X, Y, a.D, d0, dc, inv_tau, state,
-                                                                  c == 0, c == nchunks - 1, dh, st);
-            } else {
-                diff_gca_kernel<<<nblk, kDiffNT, 0, s>>>(s0, arml, ns, X, Y, a.D, d0, dc, inv_tau, dh, st,
-                                                         a.grad_dhat + (size_t)b * n, s1);
-                diff_vT_kernel<<<nblk, kDiffNT, 0, s>>>(s1, arml, X, Y, a.wy, dc, s2);
-                diff_hT_kernel<<<nblk, kDiffNT, 0, s>>>(s2, arml, X, Y, a.wx, dc, s3);
-                diff_costgrad_kernel<<<nblk, kDiffNT, 0, s>>>(gl, gr, pixl, pixr, a.theta, X, Y, a.D, d0, dc, s3,
-                                                              accl, accr,
-                                                              part + ((size_t)b * nchunks + c) * nblk * 4);
-            }
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
-        if (a.backward)
-            diff_finish_kernel<<<nblk, kDiffNT, 0, s>>>(accl, accr, n, a.grad_left + (size_t)b * n * 3,
-                                                        a.grad_right + (size_t)b * n * 3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (a.backward) {
-        diff_theta_reduce_kernel<<<1, kRedNT, 0, s>>>(part, a.B * nchunks * nblk, a.grad_theta);
-        e = cudaGetLastError();
+        diff_finish_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.accl, w.accr, n, a.grad_left, a.grad_right);
+        diff_theta_reduce_kernel<<<1, kRedNT, 0, s>>>(w.part, B * nchunks * nblk, a.grad_theta);
     }
-    return e;
+    return cudaGetLastError();
 }
 
 }  // namespace stereo
