@@ -396,43 +396,55 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         uint32_t am[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) am[j] = __ldg(armc + min(j, rows - 1) * X);
-        for (int y = 0; y < rows; y += R) {
-            uint32_t an[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) an[j] = __ldg(armc + min(y + R + j, rows - 1) * X);
-            uint32_t c[R][T::DPT], kk[R];
-            if (y + R - 1 < Y) {
-                if (!mbar_wait_warp(&full[(y % T::RS) >> 2], (y / T::RS) & 1, limit, a.err)) return;
-#pragma unroll
-                for (int j = 0; j < R; ++j) hsum(left, y + j, am[j], c[j]);
-                mbar_arrive(&empty[(y % T::RS) >> 2]);
-#pragma unroll
-                // output row r - wy reads V down to slot r - 2wy, which shares
-                // its ring slot with r + 2 when wy = 31, so each row's key is
-                // taken before the next row is pushed
-                for (int j = 0; j < R; ++j) {
-                    push(y + j, c[j]);
-                    kk[j] = vkey(y + j - wy, am[j]);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const int r = y + j;
-                    if (r < Y) {
-                        if (j == 0 && !mbar_wait_warp(&full[(r % T::RS) >> 2], (r / T::RS) & 1, limit, a.err))
-                            return;
-                        hsum(left, r, am[j], c[j]);
-                        if (j == R - 1 || r + 1 == Y) mbar_arrive(&empty[(r % T::RS) >> 2]);
-                        push(r, c[j]);
-                    }
-                    kk[j] = vkey(r - wy, am[j]);
-                }
-            }
+        auto atomics = [&](int y, const uint32_t (&kk)[R]) {
             if (g == 0 && valid) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
                     if (y + j - wy >= 0 && y + j < rows) atomicMin(key + (y + j - wy) * X, kk[j]);
             }
+        };
+        int y = 0;
+        // steps whose four rows are all inputs: no branch but the wait
+        for (; y + R - 1 < Y; y += R) {
+            uint32_t an[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) an[j] = __ldg(armc + min(y + R + j, rows - 1) * X);
+            uint32_t c[R][T::DPT], kk[R];
+            if (!mbar_wait_warp(&full[(y % T::RS) >> 2], (y / T::RS) & 1, limit, a.err)) return;
+#pragma unroll
+            for (int j = 0; j < R; ++j) hsum(left, y + j, am[j], c[j]);
+            mbar_arrive(&empty[(y % T::RS) >> 2]);
+#pragma unroll
+            // output row r - wy reads V down to slot r - 2wy, which shares
+            // its ring slot with r + 2 when wy = 31, so each row's key is
+            // taken before the next row is pushed
+            for (int j = 0; j < R; ++j) {
+                push(y + j, c[j]);
+                kk[j] = vkey(y + j - wy, am[j]);
+            }
+            atomics(y, kk);
+#pragma unroll
+            for (int j = 0; j < R; ++j) am[j] = an[j];
+        }
+        // the last input rows and the output rows that lag them
+        for (; y < rows; y += R) {
+            uint32_t an[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) an[j] = __ldg(armc + min(y + R + j, rows - 1) * X);
+            uint32_t c[R][T::DPT], kk[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int r = y + j;
+                if (r < Y) {
+                    if (j == 0 && !mbar_wait_warp(&full[(r % T::RS) >> 2], (r / T::RS) & 1, limit, a.err))
+                        return;
+                    hsum(left, r, am[j], c[j]);
+                    if (j == R - 1 || r + 1 == Y) mbar_arrive(&empty[(r % T::RS) >> 2]);
+                    push(r, c[j]);
+                }
+                kk[j] = vkey(r - wy, am[j]);
+            }
+            atomics(y, kk);
 #pragma unroll
             for (int j = 0; j < R; ++j) am[j] = an[j];
         }
