@@ -259,7 +259,10 @@ STEREO_API int stereo_tune_load(stereo_ctx *ctx, const char *path);
  *    [B][H][W][3]; theta: device float [4] = (w_AD, w_MC, l_AD, l_MC).
  *  dhat: device float [B][H][W] out; stats: device float [B][H][W][2] out
  *    (softmax maximum and sum per pixel, needed by the backward).
- * H up to 8192, W up to 4096, D up to 256, B up to 64. Asynchronous. */
+ * H up to 8192, W up to 4096, D up to 256, B up to 64. Asynchronous.
+ * The context's workspace for this form holds planes of every pair (all
+ * pairs of a batch run in each launch): about 200 bytes per pixel and pair,
+ * 70 MB for one 718x496 pair; STEREO_ENOMEM past the context's cap. */
 STEREO_API int stereo_diff_forward(stereo_ctx *ctx, int B, int W, int H, int D, const float *left,
                                    const float *right, const uint8_t *left_u8, const uint8_t *right_u8,
                                    const float *theta, float tau, float *dhat, float *stats, void *stream);
