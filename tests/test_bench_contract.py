@@ -37,3 +37,8 @@ def test_too_few_warmup_steps_are_rejected():
 def test_zero_lanes_are_rejected():
     r = _run("--steps", "1", "--warmup", "3", "--lanes", "0")
     assert r.returncode != 0 and "lanes" in r.stderr
+
+
+def test_unknown_form_is_rejected():
+    r = _run("--steps", "1", "--warmup", "3", "--forms", "batch,nothing")
+    assert r.returncode != 0 and "--forms" in r.stderr
