@@ -25,6 +25,8 @@ namespace stereo {
 namespace {
 
 constexpr int kDC = 8;   // disparities per chunk
+// pixel tiles of the kernels that sum along y (blocks of kTileX * kTileY = 256 threads)
+constexpr int kTileX = 32, kTileY = 8;
 __constant__ float kGreyW[3] = {77.f / 256.f, 150.f / 256.f, 29.f / 256.f};
 
 __global__ void diff_grey_kernel(const float *__restrict__ rgb_l, const float *__restrict__ rgb_r,
@@ -145,16 +147,19 @@ __global__ void diff_vagg_softmax_kernel(const float *__restrict__ cax, const ui
                                          float inv_tau, float *__restrict__ state, int first, int last,
                                          float *__restrict__ dhat, float *__restrict__ stats)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= X * Y) return;
-    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    // 2-D tiles of kTileX x kTileY pixels: the warps of a block walk the
+    // same anchor rows, so their vertical windows meet in L1
+    const int x = blockIdx.x * kTileX + (int)(threadIdx.x % kTileX);
+    const int y = blockIdx.y * kTileY + (int)(threadIdx.x / kTileX);
+    if (x >= X || y >= Y) return;
+    const int i = y * X + x;
+    const size_t b = blockIdx.z, n = (size_t)X * Y;   // pair
     cax += b * kDC * n;
     arm += b * n;
     ns += b * n;
     state += b * 3 * n;
     dhat += b * n;
     stats += b * 2 * n;
-    const int y = i / X, x = i - y * X;
     const uint32_t am = arm[i];
     const float inv_n = 1.f / ns[i];
     float m = first ? -INFINITY : state[3 * i], s = first ? 0.f : state[3 * i + 1],
@@ -195,9 +200,13 @@ __global__ void diff_gca_kernel(const float *__restrict__ cax, const uint32_t *_
                                 const float *__restrict__ dhat, const float *__restrict__ stats,
                                 const float *__restrict__ go, float *__restrict__ g0)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= X * Y) return;
-    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    // 2-D tiles of kTileX x kTileY pixels: the warps of a block walk the
+    // same anchor rows, so their vertical windows meet in L1
+    const int x = blockIdx.x * kTileX + (int)(threadIdx.x % kTileX);
+    const int y = blockIdx.y * kTileY + (int)(threadIdx.x / kTileX);
+    if (x >= X || y >= Y) return;
+    const int i = y * X + x;
+    const size_t b = blockIdx.z, n = (size_t)X * Y;   // pair
     cax += b * kDC * n;
     arm += b * n;
     ns += b * n;
@@ -205,7 +214,6 @@ __global__ void diff_gca_kernel(const float *__restrict__ cax, const uint32_t *_
     stats += b * 2 * n;
     go += b * n;
     g0 += b * kDC * n;
-    const int y = i / X, x = i - y * X;
     const uint32_t am = arm[i];
     const float inv_n = 1.f / ns[i];
     const float m = stats[2 * i], s = stats[2 * i + 1], e = dhat[i], gi = go[i];
@@ -229,13 +237,15 @@ __global__ void diff_gca_kernel(const float *__restrict__ cax, const uint32_t *_
 __global__ void diff_vT_kernel(const float *__restrict__ g0, const uint32_t *__restrict__ arm, int X, int Y,
                                int wy, int dc, float *__restrict__ g1)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= X * Y) return;
-    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
+    // 2-D tiles, as in diff_vagg_softmax_kernel
+    const int x = blockIdx.x * kTileX + (int)(threadIdx.x % kTileX);
+    const int yp = blockIdx.y * kTileY + (int)(threadIdx.x / kTileX);
+    if (x >= X || yp >= Y) return;
+    const int i = yp * X + x;
+    const size_t b = blockIdx.z, n = (size_t)X * Y;   // pair
     g0 += b * kDC * n;
     arm += b * n;
     g1 += b * kDC * n;
-    const int yp = i / X, x = i - yp * X;
     const int ya = max(yp - wy, 0), yb = min(yp + wy, Y - 1);
     // each anchor's arms are read once for all disparities of the chunk; per
     // disparity the sum still runs over y in ascending order
@@ -492,6 +502,8 @@ cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
     const size_t part_pair = (size_t)nchunks * nblk * 4;
     const size_t armc_n = (size_t)X * (Y + a.wy);
     const float inv_tau = 1.f / a.tau;
+    const dim3 tiles((X + kTileX - 1) / kTileX, (Y + kTileY - 1) / kTileY, B);
+    static_assert(kTileX * kTileY == kDiffNT, "one thread per pixel of a tile");
     cudaError_t e = cudaSuccess;
     // frozen supports of every pair (integer path), support sizes, float grey
     diff_grey_kernel<<<dim3(nblk, 2, B), kDiffNT, 0, s>>>(a.left, a.right, w.gl, w.gr, n);
@@ -514,13 +526,13 @@ cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
         diff_costx_kernel<<<dim3(Y, B), kDiffNT, (size_t)dc * X * 4, s>>>(w.gl, w.gr, w.pixl, w.pixr, w.arml,
                                                                           a.theta, X, Y, a.D, d0, dc, w.s0);
         if (!a.backward) {
-            diff_vagg_softmax_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s0, w.arml, w.ns, X, Y, a.D, d0, dc,
+            diff_vagg_softmax_kernel<<<tiles, kDiffNT, 0, s>>>(w.s0, w.arml, w.ns, X, Y, a.D, d0, dc,
                                                                        inv_tau, w.state, c == 0, c == nchunks - 1,
                                                                        a.dhat, a.stats);
         } else {
-            diff_gca_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s0, w.arml, w.ns, X, Y, a.D, d0, dc, inv_tau,
+            diff_gca_kernel<<<tiles, kDiffNT, 0, s>>>(w.s0, w.arml, w.ns, X, Y, a.D, d0, dc, inv_tau,
                                                               a.dhat, a.stats, a.grad_dhat, w.s1);
-            diff_vT_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s1, w.arml, X, Y, a.wy, dc, w.s2);
+            diff_vT_kernel<<<tiles, kDiffNT, 0, s>>>(w.s1, w.arml, X, Y, a.wy, dc, w.s2);
             diff_hT_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s2, w.arml, X, Y, a.wx, dc, w.s3);
             diff_costgrad_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.gl, w.gr, w.pixl, w.pixr, a.theta, X, Y, a.D,
                                                                    d0, dc, w.s3, w.accl, w.accr,
