@@ -11,7 +11,8 @@ rotate over a pool of pairs larger than the L2 cache. e2e: the same metric
 through the host-buffer entry point (host-to-device copies of both images and
 the device-to-host copy of the float map inside the timed region).
 roofline: the fused cost + aggregation + WTA kernel against the SM issue
-limit (ALU-bound; see the design doc for the per-cell operation count).
+limit (ALU-bound: 13 integer operations per (x, y, d) cell for both bases on
+the prefix formulation of Eqs. 3-9), and against its shared-memory pipe.
 
 Multi-GPU (torchrun): one independent replica per GPU on its own frames
 (weak scaling); a barrier and a max over ranks bracket the timed region.
