@@ -58,7 +58,8 @@ enum {
 
 /* Method parameters. Defaults (stereo_default_params) are the paper's values
  * (Sec. V: lambda_AD = 0.3, lambda_MC = 2.3, T = 3; Table II footnote:
- * W_x = 21, W_y = 31 per side, TC = 13) plus this build's readings. */
+ * W_x = 21, W_y = 31 per side, TC = 13) plus values for what the paper
+ * leaves open (cost scale, fill mode, downscaling). */
 typedef struct {
     double lambda_ad; /* Eq. 4, on intensities scaled to [0, 1]; 0.3 */
     double lambda_mc; /* Eq. 5; 2.3 */
