@@ -150,7 +150,8 @@ def _dist():
 
 
 def run_reference(args):
-    """The CPU oracle, as it stands, on the host cores: a bounded sample per step."""
+    """The CPU oracle, as it stands, on the host cores (OpenMP over rows on
+    every core): a bounded sample per step, scaled to whole frames."""
     world, rank, _ = _dist()
     if rank != 0:
         return
@@ -159,6 +160,7 @@ def run_reference(args):
     import oracle
     from paper_2212_00488_gb300 import scenes
     oracle.build.build()
+    cores = oracle.set_threads(0)
     s = scenes.make_scene(W_FULL, H_FULL, DMAX, PLANES, SEED)
     band = H_FULL // 8                            # 124 full-res rows per step
     fracs, times = [], []
@@ -180,28 +182,48 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": "1436x992 RGB, Dmax 145, downscale 2x (718x496, D 73), full pipeline",
                    "sample": f"{band}-row band of the frame per step"},
-        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"one {band}x{W_FULL} row band (1/8 frame) per step, single thread, "
-                                   "scaled to frames/s"},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one {band}x{W_FULL} row band (1/8 frame) per step, OpenMP over rows on "
+                                   f"{cores} threads, scaled to frames/s"},
         "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline_leg():
-    """The oracle timed on this host (rank 0, N = 1): two full frames, one thread."""
+    """The oracle timed on this host (rank 0, N = 1), as it stands: integer
+    mode with OpenMP over rows on every core (the line's value), integer mode
+    on one thread, and the FP64 mode (Eqs. 3-9 in double for both bases, on
+    every core)."""
     import numpy as np
 
     import oracle
     from paper_2212_00488_gb300 import scenes
     oracle.build.build()
     s = scenes.make_scene(W_FULL, H_FULL, DMAX, PLANES, SEED)
-    n, t0 = 2, time.perf_counter()
-    for _ in range(n):
-        oracle.pipeline(np.ascontiguousarray(s.left), np.ascontiguousarray(s.right), DMAX, oracle.Params())
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} full 1436x992/145 frames, whole pipeline, single thread"}
+    left, right = np.ascontiguousarray(s.left), np.ascontiguousarray(s.right)
+
+    def rate(n, fn):
+        t0 = time.perf_counter()
+        for _ in range(n):
+            fn()
+        return n / (time.perf_counter() - t0)
+
+    cores = oracle.set_threads(0)
+    whole = lambda: oracle.pipeline(left, right, DMAX, oracle.Params())   # noqa: E731
+    all_cores = rate(6, whole)
+    oracle.set_threads(1)
+    one = rate(2, whole)
+    oracle.set_threads(0)
+    fp64 = rate(2, lambda: oracle.wta_pair_f64(left, right, DMAX, oracle.Params()))
+    return {"value": all_cores, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"6 full 1436x992/145 frames, whole pipeline, integer mode, OpenMP over rows on "
+                      f"{cores} threads",
+            "single_thread": {"value": one, "unit": "frames/s", "cores": 1,
+                              "sample": "2 full frames, whole pipeline, integer mode, one thread"},
+            "fp64": {"value": fp64, "unit": "frames/s", "cores": cores,
+                     "sample": f"2 full frames: grey, downscale, census and arms, then the cost, both "
+                               f"aggregations and the WTA of both bases in FP64 on {cores} threads"}}
 
 
 BATCH_MENU = [(640, 480, 64), (1024, 768, 96), (1436, 992, 145), (1920, 1080, 192)]
@@ -252,7 +274,7 @@ def measure_batch(dev, stream, steps=20, warmup=3, seed=2):
 SERVE_MENU = [(640, 480, 64), (1436, 992, 145), (1920, 1080, 192)]
 
 
-def measure_serve(dev, seconds=10.0, rate=120.0, seed=4):
+def measure_serve(dev, seconds=60.0, rate=120.0, seed=4):
     """Serving form: Poisson arrivals at `rate` per second for `seconds`, each a
     single pair of a resolution drawn uniformly from the menu, device-resident
     inputs, continuous batching with an 8 GB admission cap."""
@@ -601,7 +623,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched/served/differentiable forms")
     ap.add_argument("--forms", default="batch,serve,diff",
                     help="comma-separated forms to measure after the pipeline (batch, serve, diff)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served request stream")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the served request stream")
     ap.add_argument("--tile", type=int, default=-1, help="force a tile shape of the fused kernel (-1: automatic)")
     ap.add_argument("--lanes", type=int, default=2,
                     help="library contexts (each on its own stream) that take frames in turn; with more than two "

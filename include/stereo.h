@@ -231,6 +231,17 @@ typedef struct {
  * one; both count against the memory cap. */
 STEREO_API int stereo_compute_batch(stereo_ctx *ctx, int n, const stereo_job *jobs, void *stream);
 
+/* Device bytes one frame of W x H with Dmax disparities takes in the batch
+ * workspace of stereo_compute_batch under parameters p (NULL = the defaults):
+ * its grey planes, support words, WTA keys, median and filled maps, plus a
+ * 256-byte share of the batch's tile counter. A batch's workspace is at most
+ * the sum of its frames' figures; a context created with mem_cap_bytes at
+ * least that sum runs the batch without STEREO_ENOMEM (if it holds no
+ * single-frame workspace). The caller's input and output buffers are not
+ * included. Host arithmetic only: needs no device and no context. Returns 0
+ * for parameters or a frame size the entry points reject. */
+STEREO_API size_t stereo_job_bytes(const stereo_params *p, int W, int H, int Dmax);
+
 /* Tile shape used by the last batch (-1 if none); when tune_ms is not NULL
  * it receives, for up to n tile ids, the autotuner's time of that shape in
  * ms (-1 where it did not fit or no tuning ran in that call). */

@@ -57,8 +57,16 @@ def lib():
                                                                            ctypes.c_void_p, ctypes.c_void_p,
                                                                            ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_diff.restype = _int
+        L.oracle_set_threads.argtypes = [_int]
+        L.oracle_set_threads.restype = _int
         _lib = L
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's row loops (0: every processor); returns the
+    count in effect. Results are the same for any count."""
+    return lib().oracle_set_threads(int(n))
 
 
 @dataclass
@@ -243,6 +251,36 @@ def pipeline(left_rgb, right_rgb, dmax: int, p: Params = Params()) -> Result:
     else:
         disp = dplus.copy()
     return Result(disp, dl, dr, gcp, dm, dplus, gl, gr, cl, cr, al, ar, gl_full)
+
+
+def supports(left_rgb, right_rgb, p: Params = Params()):
+    """Processed grey, census codes and arms of both images (Sec. III steps
+    1-3), the inputs of the matching cost."""
+    gl, gr = grey(left_rgb), grey(right_rgb)
+    if p.downscale:
+        gl, gr = downscale(gl), downscale(gr)
+    return (gl, census(gl), arms(gl, p.wx, p.wy, p.tc)), (gr, census(gr), arms(gr, p.wx, p.wy, p.tc))
+
+
+def wta_pair_f64(left_rgb, right_rgb, dmax: int, p: Params = Params()):
+    """FP64 mode of the matching cost, both aggregations and the WTA for both
+    bases (Eqs. 3-9 without quantisation). Returns ((D^L, best, second),
+    (D^R, best, second))."""
+    (gl, cl, al), (gr, cr, ar) = supports(left_rgb, right_rgb, p)
+    D = processed_dmax(dmax, p.downscale)
+    return wta_f64(gl, cl, gr, cr, al, D, -1, p), wta_f64(gr, cr, gl, cl, ar, D, +1, p)
+
+
+def support_size(arms_b):
+    """Cells in each anchor's cross support: the sum over the rows of its
+    vertical arm of each row's horizontal width (Eqs. 7-8)."""
+    hm, hp, vm, vp = (np.asarray(a, np.int64) for a in arms_b)
+    width = hm + hp + 1
+    Y, X = width.shape
+    cum = np.vstack([np.zeros((1, X), np.int64), np.cumsum(width, axis=0)])
+    ys = np.arange(Y)[:, None]
+    xs = np.arange(X)[None, :]
+    return cum[ys + vp + 1, xs] - cum[ys - vm, xs]
 
 
 def grey_f(rgb):

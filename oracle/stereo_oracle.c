@@ -22,6 +22,25 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads for the row loops marked "omp parallel for" below (OpenMP over
+ * rows, used only to time the oracle on all host cores). Each output element
+ * is still computed by one thread in the same order, so results do not depend
+ * on the count. n <= 0 takes every processor. Returns the count in effect
+ * (1 when built without OpenMP). */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 static int absi(int v) { return v < 0 ? -v : v; }
@@ -141,6 +160,7 @@ static void cost_plane_int(const uint8_t *gB, const uint8_t *cB, const uint8_t *
                            int64_t *Cp)
 {
     int64_t P = (int64_t)lut_ad[255] + lut_mc[6];
+    #pragma omp parallel for schedule(static)
     for (int y = 0; y < Y; ++y)
         for (int x = 0; x < X; ++x) {
             int xm = x + dir * d;
@@ -161,6 +181,7 @@ static void cost_plane_f64(const uint8_t *gB, const uint8_t *cB, const uint8_t *
                            int X, int Y, int d, int dir, double lambda_ad, double lambda_mc, double *Cp)
 {
     double P = (1.0 - exp(-1.0 / lambda_ad)) + (1.0 - exp(-6.0 / lambda_mc));
+    #pragma omp parallel for schedule(static)
     for (int y = 0; y < Y; ++y)
         for (int x = 0; x < X; ++x) {
             int xm = x + dir * d;
@@ -183,6 +204,7 @@ static void aggregate_plane_int(const int64_t *Cp, const uint8_t *hm, const uint
                                 const uint8_t *vm, const uint8_t *vp, int X, int Y,
                                 int64_t *CAx, int64_t *CA)
 {
+    #pragma omp parallel for schedule(static)
     for (int y = 0; y < Y; ++y)
         for (int x = 0; x < X; ++x) {
             size_t i = (size_t)y * X + x;
@@ -190,6 +212,7 @@ static void aggregate_plane_int(const int64_t *Cp, const uint8_t *hm, const uint
             for (int t = -(int)hm[i]; t <= (int)hp[i]; ++t) s += Cp[i + t];
             CAx[i] = s;
         }
+    #pragma omp parallel for schedule(static)
     for (int y = 0; y < Y; ++y)
         for (int x = 0; x < X; ++x) {
             size_t i = (size_t)y * X + x;
@@ -203,6 +226,7 @@ static void aggregate_plane_f64(const double *Cp, const uint8_t *hm, const uint8
                                 const uint8_t *vm, const uint8_t *vp, int X, int Y,
                                 double *CAx, double *CA)
 {
+    #pragma omp parallel for schedule(static)
     for (int y = 0; y < Y; ++y)
         for (int x = 0; x < X; ++x) {
             size_t i = (size_t)y * X + x;
@@ -210,6 +234,7 @@ static void aggregate_plane_f64(const double *Cp, const uint8_t *hm, const uint8
             for (int t = -(int)hm[i]; t <= (int)hp[i]; ++t) s += Cp[i + t];
             CAx[i] = s;
         }
+    #pragma omp parallel for schedule(static)
     for (int y = 0; y < Y; ++y)
         for (int x = 0; x < X; ++x) {
             size_t i = (size_t)y * X + x;
@@ -256,6 +281,7 @@ int oracle_wta_int(const uint8_t *gB, const uint8_t *cB, const uint8_t *gM, cons
     for (int d = 0; d < D; ++d) {
         cost_plane_int(gB, cB, gM, cM, X, Y, d, dir, lut_ad, lut_mc, Cp);
         aggregate_plane_int(Cp, hm, hp, vm, vp, X, Y, CAx, CA);
+#pragma omp parallel for schedule(static)
         for (size_t i = 0; i < n; ++i)
             if (d == 0 || CA[i] < best[i]) { best[i] = CA[i]; disp[i] = (uint8_t)d; }
     }
@@ -279,6 +305,7 @@ int oracle_wta_f64(const uint8_t *gB, const uint8_t *cB, const uint8_t *gM, cons
     for (int d = 0; d < D; ++d) {
         cost_plane_f64(gB, cB, gM, cM, X, Y, d, dir, lambda_ad, lambda_mc, Cp);
         aggregate_plane_f64(Cp, hm, hp, vm, vp, X, Y, CAx, CA);
+#pragma omp parallel for schedule(static)
         for (size_t i = 0; i < n; ++i) {
             if (CA[i] < best[i]) { second[i] = best[i]; best[i] = CA[i]; disp[i] = (uint8_t)d; }
             else if (CA[i] < second[i]) second[i] = CA[i];

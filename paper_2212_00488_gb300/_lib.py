@@ -79,6 +79,7 @@ _SIGNATURES = {
     "stereo_set_wait_limit": (_i, [_ctxp, ctypes.c_uint32]),
     "stereo_compute_batch": (_i, [_ctxp, _i, ctypes.c_void_p, _vp]),
     "stereo_batch_tile": (_i, [_ctxp, ctypes.POINTER(ctypes.c_float), _i]),
+    "stereo_job_bytes": (ctypes.c_size_t, [ctypes.POINTER(stereo_params), _i, _i, _i]),
     "stereo_tune_save": (_i, [_ctxp, ctypes.c_char_p]),
     "stereo_tune_load": (_i, [_ctxp, ctypes.c_char_p]),
     "stereo_diff_forward": (_i, [_ctxp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]),
@@ -213,6 +214,11 @@ def stereo_compute_batch(ctx, jobs, stream=0):
     """jobs: a sequence of stereo_job structures."""
     arr = (stereo_job * len(jobs))(*jobs)
     return check(ctx, load().stereo_compute_batch(ctx, len(jobs), ctypes.cast(arr, ctypes.c_void_p), stream or None))
+
+
+def stereo_job_bytes(params, W, H, dmax):
+    """Batch workspace bytes of one W x H frame (0 if the library rejects it)."""
+    return int(load().stereo_job_bytes(ctypes.byref(params) if params is not None else None, W, H, dmax))
 
 
 def stereo_batch_tile(ctx):

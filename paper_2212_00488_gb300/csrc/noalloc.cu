@@ -120,8 +120,10 @@ extern "C" int stereo_compute_noalloc(const stereo_params *params, const uint8_t
     auto u32 = [&](size_t o) { return reinterpret_cast<uint32_t *>(base + o); };
     float *dplus = ds ? reinterpret_cast<float *>(base + o_dplus) : disp_out;
 
-    if ((e = launch_grey(left_rgb, right_rgb, u8(o_gf[0]), u8(o_gf[1]), W, H, s)) == cudaSuccess &&
-        (!ds || (e = launch_downscale(u8(o_gf[0]), u8(o_gf[1]), u8(o_gs[0]), u8(o_gs[1]), W, H, s)) == cudaSuccess) &&
+    int launches = 0;
+    if ((e = ds ? launch_grey_down(left_rgb, right_rgb, u8(o_gf[0]), u8(o_gf[1]), u8(o_gs[0]), u8(o_gs[1]), W, H,
+                                   s, &launches)
+                : launch_grey(left_rgb, right_rgb, u8(o_gf[0]), u8(o_gf[1]), W, H, s)) == cudaSuccess &&
         (e = launch_support(u8(o_gs[0]), u8(o_gs[1]), u32(o_pix[0]), u32(o_pix[1]), u32(o_arm[0]), u32(o_arm[1]),
                             u32(o_armc[0]), u32(o_armc[1]), u32(o_key[0]), u32(o_key[1]), u32(o_err), X, Y, p.wx,
                             p.wy, p.tc, s)) == cudaSuccess) {

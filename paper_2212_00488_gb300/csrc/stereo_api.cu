@@ -511,10 +511,10 @@ int stereo_sync(stereo_ctx *c)
 {
     if (!c) return STEREO_EINVAL;
     DeviceGuard g(c->device);
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
-    if ((e = cudaMemcpy(c->h_err, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return cuda_fail(c, e, "device-to-host copy");
+    // the error word is read on the context's own stream, after its work
+    cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
     if (*c->h_err) return fail(c, STEREO_ETIMEOUT, "a bounded wait in the fused kernel gave up");
     return STEREO_OK;
 }
@@ -892,6 +892,19 @@ int stereo_compute_batch(stereo_ctx *c, int n, const stereo_job *jobs, void *str
     c->launches = launches;
     c->last_batch_tile = tile;
     return STEREO_OK;
+}
+
+size_t stereo_job_bytes(const stereo_params *p, int W, int H, int Dmax)
+{
+    stereo_params q;
+    if (p) q = *p; else stereo_default_params(&q);
+    if (check_params(nullptr, q) != STEREO_OK) return 0;
+    const int D = q.downscale ? (Dmax + 1) / 2 : Dmax;
+    if (W < 1 || H < 1 || W > 8192 || H > 8192 || (q.downscale && (W < 2 || H < 2)) || Dmax < 1 || D > 256 ||
+        (q.downscale ? W / 2 : W) > 4096)
+        return 0;
+    // the frame's layout plus one 256-byte share of the batch's tile counter
+    return frame_layout(q, W, H, Dmax, nullptr, nullptr) + 256;
 }
 
 int stereo_batch_tile(const stereo_ctx *c, float *tune_ms, int n)

@@ -22,12 +22,14 @@ from . import _lib
 from .stereo import Stereo, stream_handle
 
 
-def frame_bytes(W: int, H: int, downscale: bool = True, wy: int = 31) -> int:
-    """Device bytes one request holds while admitted: its output map and its
-    share of the batch workspace (grey, support words, keys, filled map)."""
-    X, Y = (W // 2, H // 2) if downscale else (W, H)
-    work = 2 * W * H + (2 * X * Y if downscale else 0) + 6 * 4 * X * Y + 2 * 4 * X * (Y + wy) + 5 * X * Y
-    return W * H * 4 + work + 16 * 256
+def frame_bytes(W: int, H: int, dmax: int, params=None) -> int:
+    """Device bytes one request holds while it runs: the library's batch
+    workspace for the frame (stereo_job_bytes) plus its float output map.
+    params: the lanes' stereo_params (None: the library's defaults)."""
+    ws = _lib.stereo_job_bytes(params, W, H, dmax)
+    if ws == 0:
+        raise ValueError(f"the library rejects a {W}x{H} frame with Dmax {dmax}")
+    return ws + W * H * 4
 
 
 class Admission:
@@ -85,11 +87,18 @@ class _Lane:
 class StereoServer:
     """Continuous batching on one GPU.
 
-    mem_cap_bytes bounds the device memory of admitted requests (outputs plus
-    workspace); lanes is the number of batches that may be on the GPU at once;
-    max_batch caps a batch (at most 32). tile fixes the fused kernel's tile
-    shape; None lets the library's autotuner time the shapes for each new
+    mem_cap_bytes bounds the device memory the server holds for requests.
+    Each of the `lanes` lanes (the batches that may be on the GPU at once) owns
+    an equal share of it: its library context is created with that share as
+    its memory cap, so the library itself refuses a batch workspace beyond it,
+    and a lane's batch takes requests only while their bytes (frame_bytes:
+    workspace plus output map) fit the share. Admission counts the same bytes
+    against the whole cap. A request larger than one share is rejected at
+    submit. max_batch caps a batch (at most 32). tile fixes the fused kernel's
+    tile shape; None lets the library's autotuner time the shapes for each new
     batch signature, which costs a few ms the first time a signature appears.
+    A batch whose fused kernel gave up a bounded wait (STEREO_ETIMEOUT) fails
+    its requests' futures with the library's error.
     """
 
     def __init__(self, device: int = 0, mem_cap_bytes: int = 8 << 30, lanes: int = 2, max_batch: int = 16,
@@ -97,19 +106,20 @@ class StereoServer:
         self.device = torch.device("cuda", device)
         self.max_batch = min(max_batch, 32)
         self.adm = Admission(mem_cap_bytes)
+        self.lane_cap = mem_cap_bytes // lanes
         self.ready = collections.deque()          # admitted, not yet on a lane
         self.lanes = []
         for _ in range(lanes):
             s = torch.cuda.Stream(self.device)
-            ln = _Lane(Stereo(device, **params), s, torch.cuda.Event())
+            ln = _Lane(Stereo(device, mem_cap_bytes=self.lane_cap, **params), s, torch.cuda.Event())
             if tile is not None:
                 _lib.stereo_set_tile(ln.st.ctx, tile)
             self.lanes.append(ln)
-        self.downscale = bool(self.lanes[0].st.params.downscale)
-        self.wy = self.lanes[0].st.params.wy
+        self.params = self.lanes[0].st.params
         self.lock = threading.Condition()
         self.latencies = []
         self.completed = 0
+        self.failed = 0
         self.batches = 0
         self._stop = False
         self._error = None
@@ -127,7 +137,10 @@ class StereoServer:
         with self.lock:
             if self._error is not None:
                 raise RuntimeError("server stopped") from self._error
-            req.nbytes = frame_bytes(W, H, self.downscale, self.wy)
+            req.nbytes = frame_bytes(W, H, dmax, self.params)
+            if req.nbytes > self.lane_cap:
+                raise ValueError(f"request needs {req.nbytes} bytes, more than a lane's share of "
+                                 f"{self.lane_cap}")
             self.adm.offer(req, req.nbytes)
             self.lock.notify()
         return fut
@@ -145,18 +158,32 @@ class StereoServer:
 
         def q(p):
             return lat[min(len(lat) - 1, int(p * len(lat)))] if lat else None
-        return {"completed": self.completed, "batches": self.batches, "p50_ms": q(0.50) and q(0.50) * 1e3,
-                "p99_ms": q(0.99) and q(0.99) * 1e3, "peak_admitted_bytes": self.adm.peak, "cap_bytes": self.adm.cap}
+        return {"completed": self.completed, "failed": self.failed, "batches": self.batches,
+                "p50_ms": q(0.50) and q(0.50) * 1e3, "p99_ms": q(0.99) and q(0.99) * 1e3,
+                "peak_admitted_bytes": self.adm.peak, "cap_bytes": self.adm.cap}
 
     # ------------------------------------------------------------ scheduler
     def _finish(self, ln: _Lane):
+        # the lane's stream is idle: reading the context's error word costs a
+        # small copy, and a bounded wait that gave up fails the whole batch
+        err = None
+        try:
+            _lib.stereo_sync(ln.st.ctx)
+        except _lib.StereoError as e:
+            err = e
         now = time.perf_counter()
         for req in ln.batch:
             req.t_done = now
-            self.latencies.append(now - req.t_submit)
             self.adm.release(req.nbytes)
-            req.future.set_result(req.out)
-        self.completed += len(ln.batch)
+            if err is None:
+                self.latencies.append(now - req.t_submit)
+                req.future.set_result(req.out)
+            else:
+                req.future.set_exception(err)
+        if err is None:
+            self.completed += len(ln.batch)
+        else:
+            self.failed += len(ln.batch)
         ln.batch = []
 
     def _launch(self, ln: _Lane, reqs):
@@ -184,8 +211,13 @@ class StereoServer:
                     self.ready.extend(r for r, _ in self.adm.admit())
                     for ln in self.lanes:
                         if not ln.batch and self.ready:
-                            n = min(self.max_batch, len(self.ready))
-                            self._launch(ln, [self.ready.popleft() for _ in range(n)])
+                            # requests in arrival order while they fit the lane's share
+                            take, used = [], 0
+                            while (self.ready and len(take) < self.max_batch
+                                   and used + self.ready[0].nbytes <= self.lane_cap):
+                                used += self.ready[0].nbytes
+                                take.append(self.ready.popleft())
+                            self._launch(ln, take)
                     busy = any(ln.batch for ln in self.lanes)
                     if self._stop and not busy and not self.ready and not self.adm.waiting:
                         return

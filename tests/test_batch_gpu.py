@@ -1,9 +1,11 @@
 """Batched form: many pairs of uneven size in one call.
 
-Each frame of a batch must equal the single-frame entry point's result for
-that frame bit-exactly (the single-frame path is itself bit-exact with the
-oracle), whatever tile shape the autotuner picks and across calls that reuse
-the captured graph with other buffers.
+Every frame of a batch is the method of Sec. III (Eqs. 3-11) on that pair, so
+each output is compared bit-exactly with the CPU oracle at every frame shape of
+the batched workload (640x480/64, 1024x768/96, 1436x992/145, 1920x1080/192).
+Frames of larger mixes are also compared with the single-frame entry point,
+whatever tile shape the autotuner picks and across calls that reuse the
+captured graph with other buffers.
 """
 import os
 import tempfile
@@ -11,6 +13,7 @@ import tempfile
 import numpy as np
 import pytest
 
+import oracle
 from paper_2212_00488_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -66,6 +69,32 @@ def _check_against_solo(frames, outs):
     solo.close()
 
 
+MENU = [(640, 480, 64), (1024, 768, 96), (1436, 992, 145), (1920, 1080, 192)]
+
+
+def test_one_frame_of_each_menu_shape_matches_the_oracle():
+    # one batch holding a frame of every shape of the batched workload; each
+    # frame's float map, D^L, D^R and GCP mask against the oracle, element by
+    # element (the largest frame first inside the persistent kernel, the
+    # smallest last, so tiles of different frames share the launch)
+    from paper_2212_00488_gb300 import Stereo
+    frames, scs = [], []
+    for i, (W, H, dmax) in enumerate(MENU):
+        sc = scenes.make_scene(W, H, dmax, planes=40, seed=500 + i)
+        scs.append(sc)
+        frames.append((torch.from_numpy(sc.left).cuda(), torch.from_numpy(sc.right).cuda(), W, H, dmax))
+    st = Stereo(0)
+    outs = _batch(st, frames)
+    st.close()
+    for sc, (_, _, W, H, dmax), o in zip(scs, frames, outs):
+        ref = oracle.pipeline(sc.left, sc.right, dmax, oracle.Params())
+        what = f"{W}x{H}/{dmax}"
+        for k, want in (("dl", ref.dl), ("dr", ref.dr), ("gcp", ref.gcp), ("disp", ref.disp)):
+            got = o[k].cpu().numpy()
+            bad = np.argwhere(got != want)
+            assert bad.size == 0, f"{what} {k}: {len(bad)} mismatches, first {bad[:5].tolist()}"
+
+
 def test_mixed_small_batch_equals_solo_and_autotunes():
     from paper_2212_00488_gb300 import Stereo, _lib
     frames = _frames([(320, 240, 32), (200, 150, 40), (401, 301, 64), (160, 120, 16), (90, 70, 9)], 3)
@@ -106,6 +135,24 @@ def test_paper_size_mix_equals_solo_with_every_fixed_tile_and_graph_update():
         for a, b in zip(outs[:4], outs_t):
             assert torch.equal(a["disp"], b["disp"]) and torch.equal(a["dl"], b["dl"])
     st.close()
+
+
+def test_job_bytes_bound_the_batch_workspace():
+    # a context whose cap is the sum of its frames' stereo_job_bytes runs the
+    # batch; a cap below the frames' layouts is refused with ENOMEM
+    from paper_2212_00488_gb300 import Stereo, _lib
+    frames = _frames([(640, 480, 64), (1024, 768, 96)], 9)
+    p = _lib.stereo_default_params()
+    need = sum(_lib.stereo_job_bytes(p, W, H, dmax) for _, _, W, H, dmax in frames)
+    st = Stereo(0, mem_cap_bytes=need)
+    outs = _batch(st, frames, tile=0)
+    st.close()
+    _check_against_solo(frames, outs)
+    small = Stereo(0, mem_cap_bytes=need // 2)
+    with pytest.raises(_lib.StereoError) as e:
+        _batch(small, frames, tile=0)
+    assert e.value.code == _lib.STEREO_ENOMEM
+    small.close()
 
 
 def test_batch_argument_errors():

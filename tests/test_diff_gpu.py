@@ -130,14 +130,20 @@ def test_autograd_l1_loss_against_finite_differences_and_determinism():
 
 
 def test_paper_shape_batch_of_four():
-    # 4 pairs of 718 x 496 with 73 disparities; pair 0 against the FP64 oracle
+    # 4 pairs of 718 x 496 with 73 disparities: every pair's dhat and input
+    # gradients against the FP64 oracle, and the batch's theta gradient against
+    # the sum of the four per-pair oracle gradients (the loss sums over pairs)
     D, tau = 73, 0.1
     u8l, u8r, fl, fr, _ = _inputs(718, 496, D, B=4, seed=11)
     go = np.random.default_rng(2).normal(size=(4, 496, 718))
     dh, gl, gr, gt = _gpu(u8l, u8r, fl, fr, D, THETA, tau, go=go)
-    odh, ogl, ogr, ogt = _oracle(u8l[0], u8r[0], fl[0], fr[0], D, THETA, tau, go=go[0])
     bound = D * (2.0 / tau) * 1e-5
-    assert np.abs(dh[0] - odh).max() <= bound
-    assert np.linalg.norm(_grey_grad(gl[0]) - ogl) <= 2e-3 * np.linalg.norm(ogl)
-    assert np.linalg.norm(_grey_grad(gr[0]) - ogr) <= 2e-3 * np.linalg.norm(ogr)
-    assert np.all(np.isfinite(gt))
+    ogt_sum = np.zeros(4)
+    for b in range(4):
+        odh, ogl, ogr, ogt = _oracle(u8l[b], u8r[b], fl[b], fr[b], D, THETA, tau, go=go[b])
+        assert np.abs(dh[b] - odh).max() <= bound, b
+        for got, want in ((_grey_grad(gl[b]), ogl), (_grey_grad(gr[b]), ogr)):
+            assert np.linalg.norm(got - want) <= 2e-3 * np.linalg.norm(want), b
+            assert np.abs(got - want).max() <= 2e-3 * np.abs(want).max(), b
+        ogt_sum += ogt
+    assert np.allclose(gt, ogt_sum, rtol=2e-3, atol=1e-4 * np.abs(ogt_sum).max()), (gt, ogt_sum)

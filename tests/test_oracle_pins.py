@@ -321,6 +321,38 @@ def test_integer_mode_matches_fp64_except_near_ties():
     assert np.array_equal(di[clear], df[clear])
 
 
+@pytest.mark.parametrize("scale", [512, 2048])
+def test_integer_mode_at_the_paper_shape_differs_only_inside_the_tie_band(scale):
+    # 1436 x 992, Dmax 145 -> 718 x 496, D 73, both bases: every pixel whose
+    # integer-mode disparity differs from the FP64 mode's (Eqs. 3-5 without
+    # quantisation) has an FP64 lead of at most 2 n / scale (n cells in its
+    # support, each term rounded by at most half a unit of 1/scale)
+    oracle.set_threads(0)
+    s = scenes.make_scene(1436, 992, 145, planes=40, seed=0)
+    p = oracle.Params(cost_scale=scale)
+    (gl, cl, al), (gr, cr, ar) = oracle.supports(s.left, s.right, p)
+    D = oracle.processed_dmax(145, 1)
+    dli = oracle.wta_int(gl, cl, gr, cr, al, D, -1, p)
+    dri = oracle.wta_int(gr, cr, gl, cl, ar, D, +1, p)
+    (dlf, bl, sl), (drf, br, sr) = oracle.wta_pair_f64(s.left, s.right, 145, p)
+    for di, df, best, second, a in ((dli, dlf, bl, sl, al), (dri, drf, br, sr, ar)):
+        band = (second - best) <= 2 * oracle.support_size(a) / scale
+        differ = di != df
+        assert not (differ & ~band).any()
+        assert band.mean() < 0.06 and differ.mean() < 1e-3
+
+
+def test_support_size_is_the_brute_force_count():
+    g = oracle.grey(scenes.make_scene(40, 30, 8, planes=3, seed=2).left)
+    a = oracle.arms(g, 5, 4, 13)
+    hm, hp, vm, vp = a
+    n = oracle.support_size(a)
+    for y in range(30):
+        for x in range(40):
+            want = sum(int(hm[y + t, x]) + int(hp[y + t, x]) + 1 for t in range(-int(vm[y, x]), int(vp[y, x]) + 1))
+            assert n[y, x] == want
+
+
 # --------------------------------------------------------------------------- cross-check, median, fill, upscale
 
 def test_crosscheck_hand_and_pairing():

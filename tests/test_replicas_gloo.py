@@ -2,9 +2,9 @@
 
 The method shards by frame (independent pairs), so N GPUs run N replicas with
 no data-path collective; the cross-rank step is the timing reduction that
-bench.py performs (sum of frames, max of times). Each rank also runs the
-CPU oracle on its own frames to check that the frame split covers every frame
-once.
+bench.py performs (sum of frames, max of times). Each rank also reports the
+frames the split gives it, and the test checks that every frame is covered
+exactly once.
 """
 import os
 import socket

@@ -27,8 +27,37 @@ def test_admission_rejects_requests_larger_than_the_cap():
         Admission(0)
 
 
-def test_frame_bytes_grows_with_the_frame():
-    small, big = frame_bytes(640, 480), frame_bytes(1920, 1080)
+@pytest.fixture(scope="module")
+def _library():
+    from paper_2212_00488_gb300 import build
+    build.build()
+
+
+def test_frame_bytes_is_the_librarys_figure_plus_the_output(_library):
+    # the library reports a frame's batch workspace (host arithmetic, no GPU);
+    # a request holds that plus its float output map
+    from paper_2212_00488_gb300 import _lib
+    p = _lib.stereo_default_params()
+    for W, H, dmax in ((640, 480, 64), (1436, 992, 145), (1920, 1080, 192), (7, 5, 3)):
+        assert frame_bytes(W, H, dmax, p) == _lib.stereo_job_bytes(p, W, H, dmax) + 4 * W * H
+        assert frame_bytes(W, H, dmax) == frame_bytes(W, H, dmax, p)
+    small, big = frame_bytes(640, 480, 64), frame_bytes(1920, 1080, 192)
     assert 0 < small < big
-    # 1436 x 992: about 12 bytes per pixel of workspace plus the 4-byte output
-    assert 14 * 1436 * 992 < frame_bytes(1436, 992) < 18 * 1436 * 992
+    # 1436 x 992 downscaled: about 12 bytes per pixel of workspace plus the output
+    assert 14 * 1436 * 992 < frame_bytes(1436, 992, 145) < 18 * 1436 * 992
+    # without downscaling every plane is at full resolution
+    p.downscale = 0
+    assert _lib.stereo_job_bytes(p, 640, 480, 64) > 35 * 640 * 480
+
+
+def test_library_rejects_what_the_entry_points_reject(_library):
+    from paper_2212_00488_gb300 import _lib
+    p = _lib.stereo_default_params()
+    assert _lib.stereo_job_bytes(p, 0, 480, 64) == 0
+    assert _lib.stereo_job_bytes(p, 640, 480, 0) == 0
+    assert _lib.stereo_job_bytes(p, 640, 480, 600) == 0      # 300 disparities after halving
+    assert _lib.stereo_job_bytes(p, 1, 480, 64) == 0         # downscaling needs W >= 2
+    p.wx = 300
+    assert _lib.stereo_job_bytes(p, 640, 480, 64) == 0
+    with pytest.raises(ValueError):
+        frame_bytes(640, 480, 0)
