@@ -33,8 +33,10 @@
 //      key = min over d of (CA << 8 | d)                             (Eq. 9)
 //    The minimum over slabs is one atomicMin per pixel and base. The packed
 //    key keeps the smallest d among equal costs, the tie rule of Step 5.
-// Vertical sums are modular uint32: differences are exact because every
-// window sum is below 2^24 (checked on the host).
+// Vertical sums are modular uint32 and kept multiplied by 256 (V << 8): a
+// difference of two ring entries is then CA << 8 exactly, because every
+// window sum is below 2^24 (checked on the host), and a key is one add of d.
+// A column's arm words of four rows arrive in one 16-byte load (armc_index).
 //
 // Every wait on an mbarrier is bounded: after a.wait_limit polls the thread
 // sets a.err and returns, so a broken hand-off ends the kernel with an error
@@ -309,15 +311,17 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     const int colc = min(max(col, 0), X - 1);
     const int dg = d0 + g * T::DPT;               // first disparity of the group
     uint32_t *key = (b ? a.key_r : a.key_l) + colc;
-    // combined arm words: row r holds the left/right arms of row r (low half)
-    // and the up/down arms of row r - wy (high half)
-    const uint32_t *armc = (b ? a.armc_r : a.armc_l) + colc;
+    // combined arm words, four rows per 16-byte quad (armc_index): row r holds
+    // the left/right arms of row r (low half) and the up/down arms of row
+    // r - wy (high half)
+    const uint4 *armq = reinterpret_cast<const uint4 *>(b ? a.armc_r : a.armc_l) + colc;
     // ring entries of this thread (an idle thread reads the last column's
     // entries and never writes)
     Vec *myring = ring + (active ? t : T::NCT - 1);
     // S element of this pixel's own column for the group's first disparity
     const SType *srow0 = sx + (g * T::DPT) * T::SWP + x + wx + (b ? g * T::DPT : 0);
     const int rows = Y + wy;                      // row steps: inputs 0..Y-1, outputs lag by wy
+    const int nquad = (rows + 3) >> 2;            // arm-word quads
 
     if (active) {
         Vec z;
@@ -331,10 +335,11 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
 
     // pair plane 0 of slot 0 at this pixel's own column (16-bit prefixes)
     const uint32_t *wrow0 = sxw + x + wx;
-    // x-window sums of one input row for this thread's disparities. With
-    // 16-bit prefixes a warp of left-base columns (kLeft) reads both
-    // disparities of a pair plane with one 32-bit load; right-base columns
-    // read disparity k at column + k, so each half on its own.
+    // x-window sums of one input row for this thread's disparities, times 256
+    // (modulo 2^32). With 16-bit prefixes a warp of left-base columns (kLeft)
+    // reads both disparities of a pair plane with one 32-bit load; right-base
+    // columns read disparity k at column + k, so each half on its own. A byte
+    // permutation takes a 16-bit difference and places it at bits 8..23.
     auto hsum = [&](auto left, int y, uint32_t am, uint32_t (&cax)[T::DPT]) {
         constexpr bool kLeft = decltype(left)::value;
         const int hi = ((am >> 8) & 0xFF) + 1, lo = am & 0xFF;
@@ -344,14 +349,14 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const uint32_t h = w[j * T::SWP + hi], l = w[j * T::SWP - lo];
-                    cax[2 * j] = (h - l) & 0xFFFFu;
-                    cax[2 * j + 1] = (h - (l & 0xFFFF0000u)) >> 16;   // no borrow from the low half
+                    cax[2 * j] = __byte_perm(h - l, 0u, 0x4104);
+                    cax[2 * j + 1] = __byte_perm(h - (l & 0xFFFF0000u), 0u, 0x4324);   // no borrow from the low half
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < T::DPT; ++k) {
                     const uint16_t *hk = reinterpret_cast<const uint16_t *>(w + (k >> 1) * T::SWP + (b ? k : 0)) + (k & 1);
-                    cax[k] = ((uint32_t)hk[2 * hi] - (uint32_t)hk[-2 * lo]) & 0xFFFFu;
+                    cax[k] = __byte_perm((uint32_t)hk[2 * hi] - (uint32_t)hk[-2 * lo], 0u, 0x4104);
                 }
             }
         } else {
@@ -359,7 +364,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
 #pragma unroll
             for (int k = 0; k < T::DPT; ++k) {
                 const SType *rk = r0 + k * (T::SWP + (b ? 1 : 0));
-                cax[k] = (uint32_t)rk[hi] - (uint32_t)rk[-lo];
+                cax[k] = ((uint32_t)rk[hi] - (uint32_t)rk[-lo]) << 8;
             }
         }
     };
@@ -387,15 +392,14 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             uint32_t best = 0xFFFFFFFFu;
 #pragma unroll
             for (int k = 0; k < T::DPT; ++k) {
-                const uint32_t kk = ((vget<T::DPT>(vh, k) - vget<T::DPT>(vl, k)) << 8) | (uint32_t)(dg + k);
+                // (V(hi) - V(lo)) << 8 is CA << 8 exactly: the key (CA << 8 | d) is one add
+                const uint32_t kk = vget<T::DPT>(vh, k) - vget<T::DPT>(vl, k) + (uint32_t)(dg + k);
                 best = (!kPart || dg + k < D) ? min(best, kk) : best;
             }
             return best;
         };
-        constexpr int R = 4;                      // rows per step
-        uint32_t am[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) am[j] = __ldg(armc + min(j, rows - 1) * X);
+        constexpr int R = 4;                      // rows per step: one arm-word quad
+        uint4 am = __ldg(armq);
         auto atomics = [&](int y, const uint32_t (&kk)[R]) {
             if (g == 0 && valid) {
 #pragma unroll
@@ -406,13 +410,11 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         int y = 0;
         // steps whose four rows are all inputs: no branch but the wait
         for (; y + R - 1 < Y; y += R) {
-            uint32_t an[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) an[j] = __ldg(armc + min(y + R + j, rows - 1) * X);
+            const uint4 an = __ldg(armq + min((y >> 2) + 1, nquad - 1) * X);
             uint32_t c[R][T::DPT], kk[R];
             if (!mbar_wait_warp(&full[(y % T::RS) >> 2], (y / T::RS) & 1, limit, a.err)) return;
 #pragma unroll
-            for (int j = 0; j < R; ++j) hsum(left, y + j, am[j], c[j]);
+            for (int j = 0; j < R; ++j) hsum(left, y + j, vget<4>(am, j), c[j]);
             mbar_arrive(&empty[(y % T::RS) >> 2]);
 #pragma unroll
             // output row r - wy reads V down to slot r - 2wy, which shares
@@ -420,17 +422,14 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             // taken before the next row is pushed
             for (int j = 0; j < R; ++j) {
                 push(y + j, c[j]);
-                kk[j] = vkey(y + j - wy, am[j]);
+                kk[j] = vkey(y + j - wy, vget<4>(am, j));
             }
             atomics(y, kk);
-#pragma unroll
-            for (int j = 0; j < R; ++j) am[j] = an[j];
+            am = an;
         }
         // the last input rows and the output rows that lag them
         for (; y < rows; y += R) {
-            uint32_t an[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) an[j] = __ldg(armc + min(y + R + j, rows - 1) * X);
+            const uint4 an = __ldg(armq + min((y >> 2) + 1, nquad - 1) * X);
             uint32_t c[R][T::DPT], kk[R];
 #pragma unroll
             for (int j = 0; j < R; ++j) {
@@ -438,15 +437,14 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 if (r < Y) {
                     if (j == 0 && !mbar_wait_warp(&full[(r % T::RS) >> 2], (r / T::RS) & 1, limit, a.err))
                         return;
-                    hsum(left, r, am[j], c[j]);
+                    hsum(left, r, vget<4>(am, j), c[j]);
                     if (j == R - 1 || r + 1 == Y) mbar_arrive(&empty[(r % T::RS) >> 2]);
                     push(r, c[j]);
                 }
-                kk[j] = vkey(r - wy, am[j]);
+                kk[j] = vkey(r - wy, vget<4>(am, j));
             }
             atomics(y, kk);
-#pragma unroll
-            for (int j = 0; j < R; ++j) am[j] = an[j];
+            am = an;
         }
     };
     // warps whose columns are all of the left base take the paired loads

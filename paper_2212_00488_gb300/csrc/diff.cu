@@ -463,8 +463,8 @@ size_t diff_layout(char *base, int X, int Y, int wy, int B, int D, DiffWs *w)
     t.pixr = (uint32_t *)take(nb * n * 4);
     t.arml = (uint32_t *)take(nb * n * 4);
     t.armr = (uint32_t *)take(nb * n * 4);
-    t.armcl = (uint32_t *)take(nb * X * (size_t)(Y + wy) * 4);
-    t.armcr = (uint32_t *)take(nb * X * (size_t)(Y + wy) * 4);
+    t.armcl = (uint32_t *)take(nb * armc_words(X, Y, wy) * 4);
+    t.armcr = (uint32_t *)take(nb * armc_words(X, Y, wy) * 4);
     t.keyl = (uint32_t *)take(nb * n * 4);                   // keys (written by the support pass)
     t.keyr = (uint32_t *)take(nb * n * 4);
     t.ns = (float *)take(nb * n * 4);                        // support size
@@ -500,7 +500,7 @@ cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
     const int nblk = (n + kDiffNT - 1) / kDiffNT;
     const int nchunks = (a.D + kDC - 1) / kDC;
     const size_t part_pair = (size_t)nchunks * nblk * 4;
-    const size_t armc_n = (size_t)X * (Y + a.wy);
+    const size_t armc_n = armc_words(X, Y, a.wy);
     const float inv_tau = 1.f / a.tau;
     const dim3 tiles((X + kTileX - 1) / kTileX, (Y + kTileY - 1) / kTileY, B);
     static_assert(kTileX * kTileY == kDiffNT, "one thread per pixel of a tile");

@@ -15,6 +15,17 @@ __host__ __device__ inline uint32_t pack_arm(int hm, int hp, int vm, int vp)
     return (uint32_t)hm | ((uint32_t)hp << 8) | ((uint32_t)vm << 16) | ((uint32_t)vp << 24);
 }
 
+// Arm words of the fused kernel, row quads interleaved: the word of row r and
+// column x sits at ((r / 4) X + x) 4 + r % 4, so one 16-byte load fetches a
+// column's words of four consecutive rows. Row r holds the left/right arms of
+// row r (low half) and the up/down arms of row r - wy (high half); rows run
+// to Y + wy - 1, rounded up to whole quads.
+__host__ __device__ inline size_t armc_index(int r, int x, int X)
+{
+    return ((size_t)(r >> 2) * X + x) * 4 + (r & 3);
+}
+inline size_t armc_words(int X, int Y, int wy) { return (size_t)X * (size_t)((Y + wy + 3) / 4) * 4; }
+
 // Tile shape of the fused kernel (see costagg.cu).
 constexpr int kRing = 64;      // V-prefix ring depth: 2*wy + 2 <= 64
 constexpr int kMaxWy = 31;
@@ -23,8 +34,7 @@ constexpr int kMaxWx = 29;
 struct CostAggArgs {
     const uint32_t *pix_l, *pix_r;   // [Y][X]
     const uint32_t *arm_l, *arm_r;   // [Y][X]
-    const uint32_t *armc_l, *armc_r; // [Y + wy][X]: low half arms of row r (left, right),
-                                     // high half arms of row r - wy (up, down)
+    const uint32_t *armc_l, *armc_r; // armc_words(X, Y, wy), laid out by armc_index
     uint32_t *key_l, *key_r;         // [Y][X] min over d of (CA << 8 | d); preset to ~0
     const uint32_t *lut_ad;          // [256] quantised AD cost (Eq. 4) by |grey difference|
     const uint32_t *lut_mc;          // [8] quantised census cost (Eq. 5) by Hamming distance

@@ -90,7 +90,7 @@ extern "C" int stereo_compute_noalloc(const stereo_params *params, const uint8_t
     for (int i = 0; i < 2; ++i) o_gs[i] = ds ? take(nl) : o_gf[i];
     for (int i = 0; i < 2; ++i) o_pix[i] = take(nl * 4);
     for (int i = 0; i < 2; ++i) o_arm[i] = take(nl * 4);
-    for (int i = 0; i < 2; ++i) o_armc[i] = take((size_t)X * (Y + p.wy) * 4);
+    for (int i = 0; i < 2; ++i) o_armc[i] = take(armc_words(X, Y, p.wy) * 4);
     for (int i = 0; i < 2; ++i) o_key[i] = take(nl * 4);
     const size_t o_dm = take(nl), o_dplus = take(nl * 4);
     if (off > kScratchBytes)

@@ -361,7 +361,7 @@ __device__ __forceinline__ void support_h(const SupportArgs &A, uint8_t *smem, i
             const size_t idx = (size_t)y * X + x;
             const uint16_t h = (uint16_t)(res[slot] | (res[NS + slot] << 8));
             arm[2 * idx] = h;
-            armc[2 * idx] = h;      // the fused kernel reads row y's left/right arms in row y
+            armc[2 * armc_index(y, x, X)] = h;   // the fused kernel reads row y's left/right arms in row y
         }
     }
 }
@@ -414,7 +414,7 @@ __device__ __forceinline__ void support_v(const SupportArgs &A, uint8_t *smem, i
             const uint16_t v = (uint16_t)(res[slot] | (res[NS + slot] << 8));
             arm[2 * ((size_t)y * X + x) + 1] = v;
             // the fused kernel reads the up/down arms of output row y in row y + wy
-            armc[2 * ((size_t)(y + wy) * X + x) + 1] = v;
+            armc[2 * armc_index(y + wy, x, X) + 1] = v;
         }
     }
 }

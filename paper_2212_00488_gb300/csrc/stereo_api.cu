@@ -178,7 +178,7 @@ size_t layout(stereo_ctx *c, char *base, int W, int H, bool staging)
     for (int i = 0; i < 2; ++i) c->gs[i] = ds ? (uint8_t *)take(nl) : c->gf[i];
     for (int i = 0; i < 2; ++i) c->pix[i] = (uint32_t *)take(nl * 4);
     for (int i = 0; i < 2; ++i) c->arm[i] = (uint32_t *)take(nl * 4);
-    for (int i = 0; i < 2; ++i) c->armc[i] = (uint32_t *)take((size_t)X * (Y + c->p.wy) * 4);
+    for (int i = 0; i < 2; ++i) c->armc[i] = (uint32_t *)take(armc_words(X, Y, c->p.wy) * 4);
     for (int i = 0; i < 2; ++i) c->key[i] = (uint32_t *)take(nl * 4);
     c->dm = (uint8_t *)take(nl);
     c->dplus_ws = (float *)take(nl * 4);
@@ -653,7 +653,7 @@ size_t frame_layout(const stereo_params &p, int W, int H, int Dmax, char *base, 
     for (int i = 0; i < 2; ++i) g.gs[i] = ds ? (uint8_t *)take(nl) : g.gf[i];
     for (int i = 0; i < 2; ++i) g.pix[i] = (uint32_t *)take(nl * 4);
     for (int i = 0; i < 2; ++i) g.arm[i] = (uint32_t *)take(nl * 4);
-    for (int i = 0; i < 2; ++i) g.armc[i] = (uint32_t *)take((size_t)X * (Y + p.wy) * 4);
+    for (int i = 0; i < 2; ++i) g.armc[i] = (uint32_t *)take(armc_words(X, Y, p.wy) * 4);
     for (int i = 0; i < 2; ++i) g.key[i] = (uint32_t *)take(nl * 4);
     g.dm = (uint8_t *)take(nl);
     g.dplus = (float *)take(nl * 4);

@@ -129,10 +129,32 @@ def test_autograd_l1_loss_against_finite_differences_and_determinism():
         assert abs(fd - g1[k]) <= 2e-3 + 2e-2 * abs(g1[k]), (k, fd, g1[k])
 
 
+def _kink_pixels(u8l, u8r, gl, gr, D, eps=1e-6):
+    """Pixels whose intensity gradient involves a cost cell at the |.| kink of
+    Eq. 4 reached by two different colours: |gL(x, y) - gR(x - d, y)| < eps for
+    some d while the RGB triples differ. The subgradient there is not unique,
+    and FP32 and FP64 may take different sides of it (equal colours give equal
+    greys in both precisions, hence the same zero subgradient)."""
+    Y, X = gl.shape
+    cl = (u8l.astype(np.int64) * np.array([65536, 256, 1])).sum(-1)
+    cr = (u8r.astype(np.int64) * np.array([65536, 256, 1])).sum(-1)
+    kl = np.zeros((Y, X), bool)
+    kr = np.zeros((Y, X), bool)
+    for d in range(min(D, X)):
+        near = (np.abs(gl[:, d:] - gr[:, :X - d]) < eps) & (cl[:, d:] != cr[:, :X - d])
+        kl[:, d:] |= near
+        kr[:, :X - d] |= near
+    return kl, kr
+
+
 def test_paper_shape_batch_of_four():
     # 4 pairs of 718 x 496 with 73 disparities: every pair's dhat and input
     # gradients against the FP64 oracle, and the batch's theta gradient against
-    # the sum of the four per-pair oracle gradients (the loss sums over pairs)
+    # the sum of the four per-pair oracle gradients (the loss sums over pairs).
+    # The input gradients are compared away from the |.| kink of Eq. 4, where
+    # the subgradient is not unique and FP32 and FP64 may take different
+    # sides: at pixels with such a cell (about 0.02 %, checked below 0.1 %)
+    # they are only required to be finite.
     D, tau = 73, 0.1
     u8l, u8r, fl, fr, _ = _inputs(718, 496, D, B=4, seed=11)
     go = np.random.default_rng(2).normal(size=(4, 496, 718))
@@ -142,8 +164,13 @@ def test_paper_shape_batch_of_four():
     for b in range(4):
         odh, ogl, ogr, ogt = _oracle(u8l[b], u8r[b], fl[b], fr[b], D, THETA, tau, go=go[b])
         assert np.abs(dh[b] - odh).max() <= bound, b
-        for got, want in ((_grey_grad(gl[b]), ogl), (_grey_grad(gr[b]), ogr)):
-            assert np.linalg.norm(got - want) <= 2e-3 * np.linalg.norm(want), b
-            assert np.abs(got - want).max() <= 2e-3 * np.abs(want).max(), b
+        kl, kr = _kink_pixels(u8l[b], u8r[b], oracle.grey_f(fl[b].astype(np.float64)),
+                              oracle.grey_f(fr[b].astype(np.float64)), D)
+        for got, want, kink in ((_grey_grad(gl[b]), ogl, kl), (_grey_grad(gr[b]), ogr, kr)):
+            assert kink.mean() < 1e-3, (b, kink.mean())
+            assert np.isfinite(got).all()
+            ok = ~kink
+            assert np.linalg.norm(got[ok] - want[ok]) <= 2e-3 * np.linalg.norm(want[ok]), b
+            assert np.abs(got[ok] - want[ok]).max() <= 2e-3 * np.abs(want).max(), b
         ogt_sum += ogt
     assert np.allclose(gt, ogt_sum, rtol=2e-3, atol=1e-4 * np.abs(ogt_sum).max()), (gt, ogt_sum)
