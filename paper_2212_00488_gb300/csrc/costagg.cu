@@ -28,7 +28,7 @@
 //  * Consumer thread (base, column) holds the slab's DS = 4 disparities and
 //    takes four rows per step:
 //      CA_x = S_q[hi] - S_q[lo] over the pixel's own left/right arms  (Eq. 7)
-//      V(y+1) = V(y) + CA_x  -> ring slot (y+1) mod 64
+//      V(y+1) = V(y) + CA_x  -> ring slot y mod 64
 //      CA(yo) = V(yo + down + 1) - V(yo - up), yo = y - wy          (Eq. 8)
 //      key = min over d of (CA << 8 | d)                             (Eq. 9)
 //    The minimum over slabs is one atomicMin per pixel and base. The packed
@@ -226,60 +226,89 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         // as this row's costs are formed, and the wait for a free slot comes
         // after the scan, so load latency and hand-off overlap the work.
         load(pw, pv0, qv0);
+        // matching cost of entry k at disparity d0 + q (its match is qv index
+        // k + DS-1 - q): one table lookup for the AD and census terms, or P
+        // outside the image (only warps that touch a border test it)
+        auto cost = [&](auto border, int k, int q) -> uint32_t {
+            constexpr bool kBorder = decltype(border)::value;
+            const uint32_t pk = pv0[k], qk = qv0[k + T::DS - 1 - q];
+            const uint32_t ad = (uint32_t)abs((int)(pk & 0xFF) - (int)(qk & 0xFF));
+            uint32_t v = lut[__popc((pk ^ qk) & 0x3F00u) * kLutPitch + ad];
+            if (kBorder) v = (inimg >> (k * T::DS + q)) & 1u ? v : P;
+            return v;
+        };
         for (int y = pw; y < Y; y += T::NPW) {
             const int s = y % T::RS;
-            uint32_t c[T::DS][T::KE];
-            uint32_t run[T::DS];
-            // the cost loop, with the out-of-image test only in warps that
-            // touch a border
-            auto form = [&](auto border) {
-                constexpr bool kBorder = decltype(border)::value;
+            if constexpr (T::S16) {
+                // 16-bit prefixes: the costs of disparities 2j and 2j+1 travel
+                // as the halves of one word (pair plane j). A lane's running
+                // sums stay below 2^16 (KE P < 2^16, checked on the host), so
+                // plain adds do; across lanes the halves add modulo 2^16 each.
+                uint32_t c2[2][T::KE], run2[2] = {0u, 0u};
+                auto form = [&](auto border) {
 #pragma unroll
-                for (int q = 0; q < T::DS; ++q) run[q] = 0;
+                    for (int k = 0; k < T::KE; ++k)
 #pragma unroll
-                for (int k = 0; k < T::KE; ++k) {
-                    const uint32_t pk = pv0[k];
+                        for (int j = 0; j < 2; ++j) {
+                            run2[j] += __byte_perm(cost(border, k, 2 * j), cost(border, k, 2 * j + 1), 0x5410);
+                            c2[j][k] = run2[j];
+                        }
+                };
+                if (all_in)
+                    form(std::false_type{});
+                else
+                    form(std::true_type{});
+                load(y + T::NPW, pv0, qv0);
+                uint32_t incl2[2] = {run2[0], run2[1]};
 #pragma unroll
-                    for (int q = 0; q < T::DS; ++q) {
-                        // match of entry k at disparity d0 + q: qv index k + DS-1 - q
-                        const uint32_t qk = qv0[k + T::DS - 1 - q];
-                        const uint32_t ad = (uint32_t)abs((int)(pk & 0xFF) - (int)(qk & 0xFF));
-                        uint32_t v = lut[__popc((pk ^ qk) & 0x3F00u) * kLutPitch + ad];
-                        if (kBorder) v = (inimg >> (k * T::DS + q)) & 1u ? v : P;
-                        run[q] += v;
-                        c[q][k] = run[q];
+                for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t u = __shfl_up_sync(0xffffffffu, incl2[j], o);
+                        if (lane >= o) incl2[j] = __vadd2(incl2[j], u);
                     }
                 }
-            };
-            if (all_in)
-                form(std::false_type{});
-            else
-                form(std::true_type{});
-            load(y + T::NPW, pv0, qv0);
-            uint32_t incl[T::DS];
-#pragma unroll
-            for (int q = 0; q < T::DS; ++q) incl[q] = run[q];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-                for (int q = 0; q < T::DS; ++q) {
-                    const uint32_t u = __shfl_up_sync(0xffffffffu, incl[q], o);
-                    if (lane >= o) incl[q] += u;
-                }
-            }
-            if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ((y / T::RS) - 1) & 1, limit, a.err)) return;
-            if constexpr (T::S16) {
+                if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ((y / T::RS) - 1) & 1, limit, a.err)) return;
                 // lanes write words KE apart (KE odd): no bank conflicts
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const uint32_t e0 = incl[2 * j] - run[2 * j], e1 = incl[2 * j + 1] - run[2 * j + 1];
+                    const uint32_t e2 = __vsub2(incl2[j], run2[j]);   // exclusive prefix of the lane's first entry
                     uint32_t *row = sxw + (s * 2 + j) * T::SWP;
 #pragma unroll
-                    for (int k = 0; k < T::KE; ++k)
-                        row[1 + lane * T::KE + k] = __byte_perm(e0 + c[2 * j][k], e1 + c[2 * j + 1][k], 0x5410);
+                    for (int k = 0; k < T::KE; ++k) row[1 + lane * T::KE + k] = __vadd2(e2, c2[j][k]);
                     if (lane == 0) row[0] = 0;
                 }
             } else {
+                uint32_t c[T::DS][T::KE];
+                uint32_t run[T::DS];
+                auto form = [&](auto border) {
+#pragma unroll
+                    for (int q = 0; q < T::DS; ++q) run[q] = 0;
+#pragma unroll
+                    for (int k = 0; k < T::KE; ++k)
+#pragma unroll
+                        for (int q = 0; q < T::DS; ++q) {
+                            run[q] += cost(border, k, q);
+                            c[q][k] = run[q];
+                        }
+                };
+                if (all_in)
+                    form(std::false_type{});
+                else
+                    form(std::true_type{});
+                load(y + T::NPW, pv0, qv0);
+                uint32_t incl[T::DS];
+#pragma unroll
+                for (int q = 0; q < T::DS; ++q) incl[q] = run[q];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                    for (int q = 0; q < T::DS; ++q) {
+                        const uint32_t u = __shfl_up_sync(0xffffffffu, incl[q], o);
+                        if (lane >= o) incl[q] += u;
+                    }
+                }
+                if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ((y / T::RS) - 1) & 1, limit, a.err)) return;
 #pragma unroll
                 for (int q = 0; q < T::DS; ++q) {
                     const uint32_t excl = incl[q] - run[q];
@@ -327,7 +356,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         Vec z;
 #pragma unroll
         for (int k = 0; k < T::DPT; ++k) vget<T::DPT>(z, k) = 0;
-        myring[0] = z;                            // V(0) = 0
+        myring[(kRing - 1) * T::NCT] = z;         // V(0) = 0 (V(r) sits in slot (r - 1) mod 64)
     }
     uint32_t V[T::DPT];
 #pragma unroll
@@ -340,17 +369,18 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     // reads both disparities of a pair plane with one 32-bit load; right-base
     // columns read disparity k at column + k, so each half on its own. A byte
     // permutation takes a 16-bit difference and places it at bits 8..23.
-    auto hsum = [&](auto left, int y, uint32_t am, uint32_t (&cax)[T::DPT]) {
+    auto hsum = [&](auto left, int slot, uint32_t am, uint32_t (&cax)[T::DPT]) {
         constexpr bool kLeft = decltype(left)::value;
         const int hi = ((am >> 8) & 0xFF) + 1, lo = am & 0xFF;
         if constexpr (T::S16) {
-            const uint32_t *w = wrow0 + (y % T::RS) * (2 * T::SWP);
+            const uint32_t *w = wrow0 + slot * (2 * T::SWP);
             if constexpr (kLeft) {
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const uint32_t h = w[j * T::SWP + hi], l = w[j * T::SWP - lo];
-                    cax[2 * j] = __byte_perm(h - l, 0u, 0x4104);
-                    cax[2 * j + 1] = __byte_perm(h - (l & 0xFFFF0000u), 0u, 0x4324);   // no borrow from the low half
+                    // both disparities of the pair at once, each half modulo 2^16
+                    const uint32_t dd = __vsub2(w[j * T::SWP + hi], w[j * T::SWP - lo]);
+                    cax[2 * j] = __byte_perm(dd, 0u, 0x4104);
+                    cax[2 * j + 1] = __byte_perm(dd, 0u, 0x4324);
                 }
             } else {
 #pragma unroll
@@ -360,7 +390,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 }
             }
         } else {
-            const SType *r0 = srow0 + (y % T::RS) * (T::DS * T::SWP);
+            const SType *r0 = srow0 + slot * (T::DS * T::SWP);
 #pragma unroll
             for (int k = 0; k < T::DPT; ++k) {
                 const SType *rk = r0 + k * (T::SWP + (b ? 1 : 0));
@@ -368,14 +398,16 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             }
         }
     };
-    auto push = [&](int y, const uint32_t (&cax)[T::DPT]) {
+    // V(y + 1) into ring slot y mod 64; the four rows of a step (y a
+    // multiple of 4) land in consecutive slots of one step base
+    auto push = [&](Vec *step_base, int j, const uint32_t (&cax)[T::DPT]) {
         Vec w;
 #pragma unroll
         for (int k = 0; k < T::DPT; ++k) {
             V[k] += cax[k];
             vget<T::DPT>(w, k) = V[k];
         }
-        if (active) myring[((y + 1) & (kRing - 1)) * T::NCT] = w;
+        if (active) step_base[j * T::NCT] = w;
     };
     // Four rows per step, one wait per step. While all four rows are inputs
     // the step has no branch but the wait, so the loads and arithmetic of
@@ -387,8 +419,8 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         // packed WTA key of output row yo over this thread's disparities
         auto vkey = [&](int yo, uint32_t am) -> uint32_t {
             const int up = (am >> 16) & 0xFF, down = am >> 24;
-            Vec vh = myring[((yo + down + 1) & (kRing - 1)) * T::NCT];
-            Vec vl = myring[((yo - up) & (kRing - 1)) * T::NCT];
+            Vec vh = myring[((yo + down) & (kRing - 1)) * T::NCT];      // V(yo + down + 1)
+            Vec vl = myring[((yo - up - 1) & (kRing - 1)) * T::NCT];    // V(yo - up)
             uint32_t best = 0xFFFFFFFFu;
 #pragma unroll
             for (int k = 0; k < T::DPT; ++k) {
@@ -412,16 +444,18 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         for (; y + R - 1 < Y; y += R) {
             const uint4 an = __ldg(armq + min((y >> 2) + 1, nquad - 1) * X);
             uint32_t c[R][T::DPT], kk[R];
-            if (!mbar_wait_warp(&full[(y % T::RS) >> 2], (y / T::RS) & 1, limit, a.err)) return;
+            const int ys = y % T::RS;             // slot of row y; rows y + j take ys + j
+            Vec *const sb = myring + (y & (kRing - 1)) * T::NCT;
+            if (!mbar_wait_warp(&full[ys >> 2], (y / T::RS) & 1, limit, a.err)) return;
 #pragma unroll
-            for (int j = 0; j < R; ++j) hsum(left, y + j, vget<4>(am, j), c[j]);
-            mbar_arrive(&empty[(y % T::RS) >> 2]);
+            for (int j = 0; j < R; ++j) hsum(left, ys + j, vget<4>(am, j), c[j]);
+            mbar_arrive(&empty[ys >> 2]);
 #pragma unroll
             // output row r - wy reads V down to slot r - 2wy, which shares
             // its ring slot with r + 2 when wy = 31, so each row's key is
             // taken before the next row is pushed
             for (int j = 0; j < R; ++j) {
-                push(y + j, c[j]);
+                push(sb, j, c[j]);
                 kk[j] = vkey(y + j - wy, vget<4>(am, j));
             }
             atomics(y, kk);
@@ -431,15 +465,17 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         for (; y < rows; y += R) {
             const uint4 an = __ldg(armq + min((y >> 2) + 1, nquad - 1) * X);
             uint32_t c[R][T::DPT], kk[R];
+            const int ys = y % T::RS;
+            Vec *const sb = myring + (y & (kRing - 1)) * T::NCT;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 const int r = y + j;
                 if (r < Y) {
-                    if (j == 0 && !mbar_wait_warp(&full[(r % T::RS) >> 2], (r / T::RS) & 1, limit, a.err))
+                    if (j == 0 && !mbar_wait_warp(&full[ys >> 2], (r / T::RS) & 1, limit, a.err))
                         return;
-                    hsum(left, r, vget<4>(am, j), c[j]);
-                    if (j == R - 1 || r + 1 == Y) mbar_arrive(&empty[(r % T::RS) >> 2]);
-                    push(r, c[j]);
+                    hsum(left, ys + j, vget<4>(am, j), c[j]);
+                    if (j == R - 1 || r + 1 == Y) mbar_arrive(&empty[ys >> 2]);
+                    push(sb, j, c[j]);
                 }
                 kk[j] = vkey(r - wy, vget<4>(am, j));
             }
@@ -564,8 +600,9 @@ template <class T>
 bool fits(const CostAggArgs &a)
 {
     if (T::XS + T::DS - 1 + 2 * a.wx > T::NE) return false;
-    // 16-bit prefixes need every horizontal window sum below 2^16
-    return !T::S16 || (uint64_t)(2 * a.wx + 1) * a.P < 65536u;
+    // 16-bit prefixes need every horizontal window sum, and every producer
+    // lane's sum of KE costs, below 2^16
+    return !T::S16 || (uint64_t)max(2 * a.wx + 1, T::KE) * a.P < 65536u;
 }
 
 
