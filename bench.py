@@ -376,28 +376,49 @@ def measure_diff(dev, steps=5, warmup=2, seed=6):
             "grad_theta": [float(v) for v in T.grad.cpu()], "steps": steps, "warmup": warmup}
 
 
-def measure_sweep(dev, frames=20, warmup=3):
-    """Timings beyond the headline workload (fused kernel and whole frame):
-    the arm caps of the paper's Table I grid that the kernel supports, the
-    other Middlebury-like shapes of Sec. V, and Dmax at 1436x992."""
+TABLE_I_WX = (5, 9, 21, 41, 61, 141)      # Table I rows (per side)
+TABLE_I_WY = (9, 11, 15, 21, 27, 31)      # Table I columns (per side)
+
+
+def _max_cost_scale(wx, wy, lad=0.3, lmc=2.3, scale=512):
+    """The default cost scale, lowered only where (2 wx + 1)(2 wy + 1) P would
+    reach 2^24 (the aggregated cost's field of the WTA key)."""
+    import math
+    unit = (1 - math.exp(-1 / lad)) + (1 - math.exp(-6 / lmc))
+    while (2 * wx + 1) * (2 * wy + 1) * (scale * unit + 1) >= 2 ** 24:
+        scale -= 16
+    return scale
+
+
+def measure_sweep(dev, frames=10, warmup=3):
+    """Timings beyond the headline workload (fused kernel and whole frame, one
+    library context): the (W_x, W_y) grid of Table I at 1436x992/145, the other
+    Middlebury-like shapes of Sec. V, and Dmax at 1436x992."""
     import torch
     from paper_2212_00488_gb300 import Stereo, _lib, scenes
 
+    pools = {}
+
+    def pool(W, H, Dmax):
+        if (W, H, Dmax) not in pools:
+            ps = [scenes.make_scene(W, H, Dmax, planes=PLANES, seed=SEED + 7 * k) for k in range(2)]
+            pools[(W, H, Dmax)] = ([torch.from_numpy(q.left).to(dev) for q in ps],
+                                   [torch.from_numpy(q.right).to(dev) for q in ps])
+        return pools[(W, H, Dmax)]
+
     def time_cfg(W, H, Dmax, **params):
-        pool = [scenes.make_scene(W, H, Dmax, planes=PLANES, seed=SEED + 7 * k) for k in range(4)]
-        L = [torch.from_numpy(p.left).to(dev) for p in pool]
-        R = [torch.from_numpy(p.right).to(dev) for p in pool]
+        L, R = pool(W, H, Dmax)
         st = Stereo(dev.index, **params)
         out = st(L[0], R[0], Dmax)
         for i in range(warmup):
-            st(L[i % 4], R[i % 4], Dmax, out=out)
+            st(L[i % 2], R[i % 2], Dmax, out=out)
         torch.cuda.synchronize()
         _lib.stereo_set_profiling(st.ctx, True)
         stream = torch.cuda.current_stream(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(frames):
-            st(L[i % 4], R[i % 4], Dmax, out=out)
+            st(L[i % 2], R[i % 2], Dmax, out=out)
         e1.record(stream)
         torch.cuda.synchronize()
         ms, _ = _lib.stereo_stage_ms(st.ctx)
@@ -407,11 +428,14 @@ def measure_sweep(dev, frames=20, warmup=3):
         return {"W": W, "H": H, "Dmax": Dmax, **params, "frame_ms": round(frame_ms, 4),
                 "fps": round(1e3 / frame_ms, 1), "kernel_ms": round(ms[_lib.STAGE_COSTAGG], 4), "tile": tile}
 
-    window = [time_cfg(W_FULL, H_FULL, DMAX, wx=wx, wy=wy) for wx in (5, 9, 21, 29) for wy in (9, 11, 15, 21, 27, 31)]
+    window = [time_cfg(W_FULL, H_FULL, DMAX, wx=wx, wy=wy, cost_scale=_max_cost_scale(wx, wy))
+              for wx in TABLE_I_WX for wy in TABLE_I_WY]
     shapes = [time_cfg(W, H, D) for W, H, D in ((1436, 992, 145), (1482, 994, 128), (1444, 960, 380))]
     dmax = [time_cfg(W_FULL, H_FULL, D) for D in (64, 128, 145, 256, 380, 511)]
     return {"frames": frames, "warmup": warmup, "window": window, "shapes": shapes, "dmax": dmax,
-            "note": "arm caps per side; the Table I caps 41, 61, 141 exceed the kernel's wx <= 29"}
+            "note": "arm caps per side (Table I grid); cost_scale lowered from 512 only where a window sum "
+                    "could reach 2^24: " + ", ".join(f"wx {w['wx']} wy {w['wy']} -> {w['cost_scale']}"
+                                                     for w in window if w["cost_scale"] != 512)}
 
 
 def run_ours(args):
@@ -448,10 +472,22 @@ def run_ours(args):
             outs.append(ctx_(left[0], right[0], DMAX))
     torch.cuda.synchronize()
 
+    isolate = {"on": False}
+
     def frame(i):
         ctx_, s_ = lanes[i % nl]
+        # a profiled frame (lane 0, every PROFILE_EVERY-th of its frames) runs
+        # with the other lanes held back, so its per-stage events time the
+        # kernels rather than their wait for SMs the other lanes hold
+        alone = isolate["on"] and i % nl == 0 and (i // nl) % PROFILE_EVERY == 0
+        if alone:
+            for s2 in streams[1:]:
+                s_.wait_stream(s2)
         with torch.cuda.stream(s_):
             ctx_(left[i % POOL], right[i % POOL], DMAX, out=outs[i % nl])
+        if alone:
+            for s2 in streams[1:]:
+                s2.wait_stream(s_)
         return _lib.stereo_last_launch_count(ctx_.ctx)
 
     for i in range(args.warmup):
@@ -474,8 +510,10 @@ def run_ours(args):
     e0.record(stream)
     for s_ in streams[1:]:
         s_.wait_event(e0)
+    isolate["on"] = nl > 1
     for i in range(args.steps):
         launches += frame(i)
+    isolate["on"] = False
     for s_ in streams[1:]:
         stream.wait_stream(s_)
     e1.record(stream)
@@ -580,8 +618,9 @@ def run_ours(args):
                          "ops_per_cell": OPS_PER_CELL, "cells_per_launch": cells,
                          "kernel_ms": stage_ms[_lib.STAGE_COSTAGG], "frames_timed": nframes,
                          "kernel_timer": f"CUDA events around each stage of every {PROFILE_EVERY}th frame of "
-                                         f"lane 0 in the timed loop, on the stream the kernels run on (the other "
-                                         f"lanes' kernels share the SMs meanwhile)",
+                                         f"lane 0 in the timed loop, on the stream the kernels run on; those "
+                                         f"frames run with the other lanes' streams held back (cross-stream "
+                                         f"waits), so the events time the kernels, not a wait for SMs",
                          "kernel_ms_one_lane": stage_alone[_lib.STAGE_COSTAGG],
                          "frac_one_lane": OPS_PER_CELL * cells / (stage_alone[_lib.STAGE_COSTAGG] / 1e3) / peak_ops,
                          "tile": _lib.stereo_get_tile(st.ctx, W_FULL, H_FULL, DMAX)},
@@ -602,7 +641,7 @@ def run_ours(args):
                 line["forms"]["serve"] = measure_serve(dev, seconds=args.serve_seconds)
             if "diff" in forms:
                 line["forms"]["diff"] = measure_diff(dev)
-        if args.sweep:
+        if not args.no_sweep:
             line["sweep"] = measure_sweep(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
@@ -628,8 +667,8 @@ def main():
     ap.add_argument("--lanes", type=int, default=2,
                     help="library contexts (each on its own stream) that take frames in turn; with more than two "
                          "the fused kernel's event time in the timed loop includes waiting for the SMs")
-    ap.add_argument("--sweep", action="store_true",
-                    help="also time the arm-cap grid, other frame shapes and Dmax (about a minute)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the timings of the Table I arm-cap grid, other frame shapes and Dmax (about 20 s)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

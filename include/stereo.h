@@ -64,7 +64,7 @@ typedef struct {
     double lambda_ad; /* Eq. 4, on intensities scaled to [0, 1]; 0.3 */
     double lambda_mc; /* Eq. 5; 2.3 */
     int tc;           /* arm brightness threshold delta (strict <), Sec. III-C; 13 */
-    int wx;           /* horizontal arm cap per side, 1..29; 21 */
+    int wx;           /* horizontal arm cap per side, 0..141 (Table I); 21 */
     int wy;           /* vertical arm cap per side, 1..31; 31 */
     int t_fill;       /* T of the bilateral estimation (Sec. III-E); 3 */
     int downscale;    /* 1: K = 2, m = 1 mean-pool with Dmax halved (Sec. III-A); 0: none */
@@ -191,13 +191,16 @@ STEREO_API int stereo_last_launch_count(const stereo_ctx *ctx);
 
 /* Tile shapes of the fused cost + aggregation + WTA kernel (columns per base
  * x disparities per CTA, row-prefix width); every consumer thread holds one
- * column and the 4 disparities of its tile:
- * 0: 104x4 16-bit, 1: 104x4 16-bit for wx up to 29, 2: 104x4 32-bit,
- * 3: 104x4 32-bit for wx up to 29, 4: 64x4 16-bit.
- * 16-bit row prefixes need (2*wx+1) times the largest matching cost below
- * 2^16. Every shape gives the same result; they differ only in speed. A
- * compute with a shape that does not fit the parameters fails with EINVAL. */
-#define STEREO_NUM_TILES 5
+ * column and 4 disparities of its tile:
+ * 0: 104x4 16-bit for wx up to 26, 1: 104x4 16-bit for wx up to 58,
+ * 2: 104x4 32-bit for wx up to 26, 3: 104x4 32-bit for wx up to 58,
+ * 4: 64x4 16-bit, 5: 100x4 16-bit with 12 row-prefix producer warps
+ * instead of 8, 6: 48x8 32-bit (slabs of 8 disparities, two threads per
+ * column), 7: 88x4 32-bit for wx up to 141 (the wide windows of Table I).
+ * 16-bit row prefixes need max(2*wx+1, 7) times the largest matching cost
+ * below 2^16. Every shape gives the same result; they differ only in speed.
+ * A compute with a shape that does not fit the parameters fails with EINVAL. */
+#define STEREO_NUM_TILES 8
 
 /* Fixes the tile shape used by later computes on this context (-1 = pick
  * automatically from the frame shape and the SM count, the default).

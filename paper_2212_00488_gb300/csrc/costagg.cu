@@ -200,7 +200,8 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         // per-lane constants: clamped load offsets and, per (entry, disparity),
         // whether the pixel and its match lie in the image
         int offl[T::KE], offr[T::KE + T::DS - 1];
-        uint32_t inimg = 0;
+        using Mask = typename std::conditional<(T::KE * T::DS > 32), uint64_t, uint32_t>::type;
+        Mask inimg = 0;
 #pragma unroll
         for (int k = 0; k < T::KE; ++k) offl[k] = min(max(xb + k, 0), X - 1);
 #pragma unroll
@@ -209,8 +210,8 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         for (int k = 0; k < T::KE; ++k)
 #pragma unroll
             for (int q = 0; q < T::DS; ++q)
-                if (xb + k >= d0 + q && xb + k < X) inimg |= 1u << (k * T::DS + q);
-        const bool all_in = __all_sync(0xffffffffu, inimg == (1u << (T::KE * T::DS)) - 1u);
+                if (xb + k >= d0 + q && xb + k < X) inimg |= (Mask)1 << (k * T::DS + q);
+        const bool all_in = __all_sync(0xffffffffu, inimg == (Mask)(~(Mask)0 >> (8 * sizeof(Mask) - T::KE * T::DS)));
         // pixels of one row: the lane's KE entries and their KE + DS - 1 matches
         uint32_t pv0[T::KE], qv0[T::KE + T::DS - 1];
         auto load = [&](int y, uint32_t (&pv)[T::KE], uint32_t (&qv)[T::KE + T::DS - 1]) {
@@ -432,7 +433,15 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         };
         constexpr int R = 4;                      // rows per step: one arm-word quad
         uint4 am = __ldg(armq);
-        auto atomics = [&](int y, const uint32_t (&kk)[R]) {
+        auto atomics = [&](int y, uint32_t (&kk)[R]) {
+            // the G threads of a column (adjacent lanes) combine their
+            // disparity groups' minima; one atomic per column and row
+            if constexpr (T::G > 1) {
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+#pragma unroll
+                    for (int o = 1; o < T::G; o <<= 1) kk[j] = min(kk[j], __shfl_xor_sync(0xffffffffu, kk[j], o));
+            }
             if (g == 0 && valid) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
@@ -574,10 +583,20 @@ __global__ void __launch_bounds__(T::NT, 1) costagg_batch_kernel(const __grid_co
 // CTA per SM; the ring of 64 prefix rows per (column, disparity, base)
 // dominates shared memory. Every shape gives the same keys.
 using T0 = Tile<104, 4, 5, 8, true, 4, 8>;    // wx <= 26, window sums < 2^16
-using T1 = Tile<104, 4, 7, 8, true, 4, 8>;    // wx <= 29, window sums < 2^16
+using T1 = Tile<104, 4, 7, 8, true, 4, 8>;    // wx <= 58, window sums < 2^16
 using T2 = Tile<104, 4, 5, 4, false, 4, 4>;   // wx <= 26, 32-bit prefixes
-using T3 = Tile<104, 4, 7, 4, false, 4, 4>;   // wx <= 29, 32-bit prefixes
+using T3 = Tile<104, 4, 7, 4, false, 4, 4>;   // wx <= 58, 32-bit prefixes
 using T4 = Tile<64, 4, 5, 8, true, 4, 8>;     // narrow frames, window sums < 2^16
+// 100 columns leave room for 12 producer warps and row slots (19 warps per
+// SM); at 718 columns every slab of a 145-disparity frame takes 8 strips,
+// 152 CTAs
+using T5 = Tile<100, 4, 5, 12, true, 4, 12>;
+// slabs of 8 disparities: two threads per column, 32-bit prefixes (the
+// batch autotuner's deeper slab)
+using T6 = Tile<48, 8, 5, 4, false, 4, 4>;
+// wide horizontal windows (Table I: W_x up to 141 per side), wx <= 162,
+// 32-bit prefixes
+using T7 = Tile<88, 4, 13, 4, false, 4, 4>;
 
 template <class T> struct Tag { using type = T; };
 
@@ -591,10 +610,13 @@ bool with_tile(int id, F &&f)
     case 2: f(Tag<T2>{}); return true;
     case 3: f(Tag<T3>{}); return true;
     case 4: f(Tag<T4>{}); return true;
+    case 5: f(Tag<T5>{}); return true;
+    case 6: f(Tag<T6>{}); return true;
+    case 7: f(Tag<T7>{}); return true;
     default: return false;
     }
 }
-static_assert(kNumTiles == 5, "tile ids 0..4");
+static_assert(kNumTiles == 8, "tile ids 0..7");
 
 template <class T>
 bool fits(const CostAggArgs &a)

@@ -29,7 +29,7 @@ inline size_t armc_words(int X, int Y, int wy) { return (size_t)X * (size_t)((Y 
 // Tile shape of the fused kernel (see costagg.cu).
 constexpr int kRing = 64;      // V-prefix ring depth: 2*wy + 2 <= 64
 constexpr int kMaxWy = 31;
-constexpr int kMaxWx = 29;
+constexpr int kMaxWx = 141;    // the largest W_x of Table I
 
 struct CostAggArgs {
     const uint32_t *pix_l, *pix_r;   // [Y][X]
@@ -74,7 +74,7 @@ cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, si
 }
 
 // Number of tile shapes of the fused kernel (ids 0 .. kNumTiles-1).
-constexpr int kNumTiles = 5;
+constexpr int kNumTiles = 8;
 int costagg_pick(const CostAggArgs &a, int nsm);
 bool costagg_fits(const CostAggArgs &a, int tile);
 

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kGDX * kGDY) grey_down_kernel(
 }
 
 // Support data in two passes, each with a halo only along its own axis.
-//  Pass H: rows of kHX pixels (plus kMaxWx + 7 pixels each side and one row
+//  Pass H: rows of kHX pixels (plus wx + 7 pixels each side and one row
 //  above and below): census code and left/right arms; grey | census << 8 goes
 //  to the pixel word, the left/right arms to the low half of the arm words.
 //  Pass V: columns of kVY pixels (plus kMaxWy + 7 rows above and below): up/down
@@ -207,7 +207,7 @@ __device__ __forceinline__ unsigned arm_lim(int tc)
 
 // Queue entry of an arm that goes on past its first chunk: the pixel's
 // offset in the tile (12 bits), its output slot (11 bits), the direction
-// (1 bit: 0 towards lower coordinates) and the cap (5 bits).
+// (1 bit: 0 towards lower coordinates) and the cap (8 bits).
 __device__ __forceinline__ uint32_t arm_entry(int toff, int slot, int dir, int cap)
 {
     return (uint32_t)toff | ((uint32_t)slot << 12) | ((uint32_t)dir << 23) | ((uint32_t)cap << 24);
@@ -270,13 +270,13 @@ constexpr int kHX = 256;   // pass H: outputs per row tile (one column per threa
 constexpr int kHY = 4;     // pass H: rows per CTA
 constexpr int kVX = 32;    // pass V: columns per CTA
 constexpr int kVY = 16;    // pass V: outputs per column tile
-constexpr int kHXH = kMaxWx + kArmChunk - 1;   // pass H halo (>= 2, the census reach)
+constexpr int kHXH = kMaxWx + kArmChunk - 1;   // pass H halo at the largest cap (wx + 7 at run time)
 constexpr int kVYH = kMaxWy + kArmChunk - 1;   // pass V halo
 static_assert(kHX == kSupNT, "pass H: one column per thread");
 static_assert(kSupNT % kVX == 0 && kVY % (kSupNT / kVX) == 0, "pass V: whole rows per thread");
 static_assert((kHX + 2 * kHXH) * (kHY + 2) < 4096 && kVX * (kVY + 2 * kVYH) < 4096, "tile offsets take 12 bits");
 static_assert(kHY * kHX <= 2048 && kVY * kVX <= 2048, "output slots take 11 bits");
-static_assert(kMaxWx < 32 && kMaxWy < 32, "caps take 5 bits");
+static_assert(kMaxWx < 256 && kMaxWy < 256, "caps take 8 bits");
 
 // Shared memory of one pass: tile, arm lengths [2][slots], queue [2 * slots], count.
 __host__ __device__ constexpr int sup_tile_bytes(int tile, int slots)
@@ -302,10 +302,13 @@ __device__ __forceinline__ void support_h(const SupportArgs &A, uint8_t *smem, i
     uint16_t *arm = reinterpret_cast<uint16_t *>(bz ? A.arm_r : A.arm_l);
     uint16_t *armc = reinterpret_cast<uint16_t *>(bz ? A.armc_r : A.armc_l);
     uint32_t *key = bz ? A.key_r : A.key_l;
-    constexpr int hx = kHXH, TW = kHX + 2 * hx, TH = kHY + 2, NS = kHY * kHX;
+    // the staged row holds the tile's pixels and wx + 7 more on each side
+    // (the first chunk of an arm at its cap reads 7 beyond it; >= 2 for census)
+    const int hx = wx + kArmChunk - 1, TW = kHX + 2 * hx;
+    constexpr int TH = kHY + 2, NS = kHY * kHX;
     uint8_t *tile = smem;
-    uint8_t *res = smem + (TW * TH + 15) / 16 * 16;              // [2][NS]
-    uint32_t *q = reinterpret_cast<uint32_t *>(res + 2 * NS);   // [2 NS]
+    uint8_t *res = smem + ((kHX + 2 * kHXH) * TH + 15) / 16 * 16;   // [2][NS]
+    uint32_t *q = reinterpret_cast<uint32_t *>(res + 2 * NS);       // [2 NS]
     int *nq = reinterpret_cast<int *>(q + 2 * NS);
     const int x0 = bx * kHX, y0 = by * kHY;
     if ((bx | by | bz | threadIdx.x) == 0) *A.err = 0u;

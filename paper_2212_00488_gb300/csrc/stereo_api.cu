@@ -613,6 +613,7 @@ int stereo_get_tile(stereo_ctx *c, int W, int H, int Dmax)
     a.D = c->p.downscale ? (Dmax + 1) / 2 : Dmax;
     a.wx = c->p.wx;
     a.wy = c->p.wy;
+    a.P = c->P;
     return costagg_pick(a, c->num_sms);
 }
 

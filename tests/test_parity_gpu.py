@@ -150,6 +150,37 @@ def test_parameter_variants(wx, wy, tc, scale):
     _compare(_run_gpu(s.left, s.right, 24, p), oracle.pipeline(s.left, s.right, 24, p), f"wx{wx} wy{wy}")
 
 
+@pytest.mark.parametrize("wx,wy,scale", [(41, 31, 512), (61, 31, 512), (141, 27, 512), (141, 31, 480)])
+def test_wide_windows_of_table_I(wx, wy, scale):
+    # the W_x of Table I beyond 26 per side need the wider prefix tiles; flat
+    # blocks 320 pixels wide let the horizontal arms run to the cap. At
+    # wx = 141, wy = 31 a window sum can reach (283 * 63) P, which needs a cost
+    # scale below 497 for the 24-bit aggregated cost of the WTA key
+    rng = np.random.default_rng(wx + wy)
+    W, H, shift = 420, 90, 5
+    base = np.kron(rng.integers(40, 220, size=(H // 45 + 1, (W + shift) // 320 + 2)), np.ones((45, 320)))
+    img = np.clip(base[:H, :W + shift] + rng.integers(-2, 3, size=(H, W + shift)), 0, 255).astype(np.uint8)
+    left = np.ascontiguousarray(np.repeat(img[:, shift:, None], 3, axis=2))
+    right = np.ascontiguousarray(np.repeat(img[:, :W, None], 3, axis=2))
+    p = _params(downscale=0, wx=wx, wy=wy, cost_scale=scale)
+    r = oracle.pipeline(left, right, 16, p)
+    assert max(int(r.arms_l[0].max()), int(r.arms_l[1].max())) == wx     # arms reach the cap
+    _compare(_run_gpu(left, right, 16, p), r, f"wx{wx} wy{wy}")
+
+
+def test_key_range_is_checked():
+    # (2 wx + 1)(2 wy + 1) P must stay below 2^24: wx = 141, wy = 31 at the
+    # default scale is refused, one step lower in wy or scale is accepted
+    from paper_2212_00488_gb300 import Stereo, _lib
+    with pytest.raises(_lib.StereoError) as e:
+        Stereo(0, wx=141, wy=31)
+    assert e.value.code == _lib.STEREO_EINVAL
+    Stereo(0, wx=141, wy=27).close()
+    Stereo(0, wx=141, wy=31, cost_scale=480).close()
+    with pytest.raises(_lib.StereoError):
+        Stereo(0, wx=142)
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_fill_variants(mode):
     # the prior-art fills of Sec. III-E (Fig. 5), downscaled so the scale-up
@@ -277,7 +308,7 @@ def test_argument_errors():
     assert e.value.code == _lib.STEREO_ENOMEM
     small.close()
     with pytest.raises(_lib.StereoError):
-        Stereo(0, wx=40)            # beyond the supported arm cap
+        Stereo(0, wx=200)           # beyond the supported arm cap
     with pytest.raises(_lib.StereoError):
         Stereo(0, cost_scale=1 << 14)   # aggregated costs would overflow the 24-bit key
     with pytest.raises(_lib.StereoError):
