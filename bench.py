@@ -38,6 +38,9 @@ POOL = 20                       # 20 pairs x 8.5 MB = 171 MB > 126 MB of L2
 PROFILE_EVERY = 10              # per-stage CUDA events on every 10th timed frame
 PAPER_FPS = 40.0                # Table II, GTX 780 Ti (context only)
 OPS_PER_CELL = 13               # algorithmic integer operations per (x, y, d) cell, both bases
+DIFF_EXPS_PER_CELL = 9          # differentiable form, forward + backward: exp per cell
+DIFF_FLOPS_PER_CELL = 48        # differentiable form: flops per cell besides the window sums
+SFU_PER_SM = 16                 # exp (MUFU) results per SM and clock
 SM_COUNT_NOMINAL = 152
 LANES_PER_SM = 128              # 4 SM sub-partitions x 32 lanes issue one warp instruction per clock each
 
@@ -369,11 +372,36 @@ def measure_diff(dev, steps=5, warmup=2, seed=6):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # mean spans of the frozen supports (the library's own arms of each pair)
+    sx = sy = 0.0
+    for b in range(B):
+        st(UL[b].contiguous(), UR[b].contiguous(), D)
+        arms = st.debug_planes(W, H)["arms_l"].cpu().numpy().view(np.uint32)
+        sx += float(((arms & 0xFF) + ((arms >> 8) & 0xFF) + 1).mean()) / B
+        sy += float((((arms >> 16) & 0xFF) + (arms >> 24) + 1).mean()) / B
     st.close()
+    cells = B * W * H * D
+    exps = DIFF_EXPS_PER_CELL * cells
+    adds = (DIFF_FLOPS_PER_CELL + 3 * (sx + sy)) * cells
+    props = torch.cuda.get_device_properties(dev)
+    peaks, _ = _peaks()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    alu_peak = props.multi_processor_count * LANES_PER_SM * clk
+    sfu_peak = props.multi_processor_count * SFU_PER_SM * clk
+    floor_s = max(adds / alu_peak, exps / sfu_peak)
     return {"workload": "4 pairs 718x496 FP32, D 73, soft-argmin tau 0.1, L1 loss, forward + backward",
             "value": B / (ms / 1e3), "unit": "pairs/s (forward + backward)", "ms_per_step": ms,
             "mde_per_s": B * W * H * D / (ms / 1e3), "loss": float(loss.item()),
-            "grad_theta": [float(v) for v in T.grad.cpu()], "steps": steps, "warmup": warmup}
+            "grad_theta": [float(v) for v in T.grad.cpu()], "steps": steps, "warmup": warmup,
+            "roofline": {"bound": "alu", "unit": "ms per step", "achieved_ms": ms, "floor_ms": floor_s * 1e3,
+                         "frac": floor_s * 1e3 / ms, "cells": cells, "exps_per_cell": DIFF_EXPS_PER_CELL,
+                         "flops_per_cell": DIFF_FLOPS_PER_CELL + 3 * (sx + sy), "mean_x_span": sx,
+                         "mean_y_span": sy,
+                         "peak_source": f"{props.multi_processor_count} SMs x ({LANES_PER_SM} lanes for adds and "
+                                        f"multiplies, {SFU_PER_SM} for exp) x {clk / 1e6:.0f} MHz",
+                         "work": "per (x, y, d) cell, forward and backward: 9 exp, "
+                                 f"{DIFF_FLOPS_PER_CELL} other flops, and the window sums three times along "
+                                 "x and y (forward, the backward's recompute, the adjoint)"}}
 
 
 TABLE_I_WX = (5, 9, 21, 41, 61, 141)      # Table I rows (per side)
