@@ -460,7 +460,9 @@ def measure_sweep(dev, frames=10, warmup=3):
               for wx in TABLE_I_WX for wy in TABLE_I_WY]
     shapes = [time_cfg(W, H, D) for W, H, D in ((1436, 992, 145), (1482, 994, 128), (1444, 960, 380))]
     dmax = [time_cfg(W_FULL, H_FULL, D) for D in (64, 128, 145, 256, 380, 511)]
+    scale = [time_cfg(W_FULL, H_FULL, DMAX, cost_scale=cs) for cs in (512, 2048)]
     return {"frames": frames, "warmup": warmup, "window": window, "shapes": shapes, "dmax": dmax,
+            "cost_scale": scale,
             "note": "arm caps per side (Table I grid); cost_scale lowered from 512 only where a window sum "
                     "could reach 2^24: " + ", ".join(f"wx {w['wx']} wy {w['wy']} -> {w['cost_scale']}"
                                                      for w in window if w["cost_scale"] != 512)}

@@ -135,7 +135,7 @@ struct Tile {
     static_assert(!S16 || (DS == 4 && G == 1), "pair planes hold the slab's four disparities");
     static_assert(KE % 2 == 1, "odd KE keeps the producer lanes' strided stores in distinct banks");
     static_assert(NT <= 1024, "");
-    static_assert(RS >= NPW, "every producer warp needs a slot of its own");
+    static_assert(RS == NPW, "producer warp p owns row slot p");
     static_assert(RS % 4 == 0, "slots are handed over in row quads");
     static_assert(BYTES <= 232448, "tile exceeds shared memory");
 };
@@ -193,7 +193,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     __syncthreads();
 
     if (t >= T::NCTP) {
-        // ======================= producers: warp pw fills rows pw, pw+4, ...
+        // ======================= producers: warp pw fills rows pw, pw + NPW, ... in slot pw
         const int pw = (t - T::NCTP) >> 5;
         const uint32_t P = a.P;
         const int xb = x0 - wx + lane * T::KE;      // x of this lane's first entry
@@ -238,8 +238,9 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             if (kBorder) v = (inimg >> (k * T::DS + q)) & 1u ? v : P;
             return v;
         };
-        for (int y = pw; y < Y; y += T::NPW) {
-            const int s = y % T::RS;
+        uint32_t ph = 1;                            // parity of the empty phase to wait for
+        const int s = pw;                           // this warp's row slot
+        for (int y = pw; y < Y; y += T::NPW, ph ^= 1u) {
             if constexpr (T::S16) {
                 // 16-bit prefixes: the costs of disparities 2j and 2j+1 travel
                 // as the halves of one word (pair plane j). A lane's running
@@ -269,7 +270,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                         if (lane >= o) incl2[j] = __vadd2(incl2[j], u);
                     }
                 }
-                if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ((y / T::RS) - 1) & 1, limit, a.err)) return;
+                if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ph, limit, a.err)) return;
                 // lanes write words KE apart (KE odd): no bank conflicts
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
@@ -309,7 +310,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                         if (lane >= o) incl[q] += u;
                     }
                 }
-                if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ((y / T::RS) - 1) & 1, limit, a.err)) return;
+                if (y >= T::RS && !mbar_wait_warp(&empty[s >> 2], ph, limit, a.err)) return;
 #pragma unroll
                 for (int q = 0; q < T::DS; ++q) {
                     const uint32_t excl = incl[q] - run[q];
@@ -433,7 +434,8 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         };
         constexpr int R = 4;                      // rows per step: one arm-word quad
         uint4 am = __ldg(armq);
-        auto atomics = [&](int y, uint32_t (&kk)[R]) {
+        auto atomics = [&](auto inputs, int y, uint32_t (&kk)[R]) {
+            constexpr bool kInputs = decltype(inputs)::value;   // rows y .. y+3 all exist
             // the G threads of a column (adjacent lanes) combine their
             // disparity groups' minima; one atomic per column and row
             if constexpr (T::G > 1) {
@@ -445,17 +447,25 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             if (g == 0 && valid) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
-                    if (y + j - wy >= 0 && y + j < rows) atomicMin(key + (y + j - wy) * X, kk[j]);
+                    if (y + j - wy >= 0 && (kInputs || y + j < rows)) atomicMin(key + (y + j - wy) * X, kk[j]);
             }
         };
         int y = 0;
+        int ys = 0;                               // slot of row y (rows y + j take ys + j)
+        uint32_t ph = 0;                          // parity of the full phase of those slots
+        auto next_slots = [&]() {
+            ys += R;
+            if (ys == T::RS) {
+                ys = 0;
+                ph ^= 1u;
+            }
+        };
         // steps whose four rows are all inputs: no branch but the wait
         for (; y + R - 1 < Y; y += R) {
             const uint4 an = __ldg(armq + min((y >> 2) + 1, nquad - 1) * X);
             uint32_t c[R][T::DPT], kk[R];
-            const int ys = y % T::RS;             // slot of row y; rows y + j take ys + j
             Vec *const sb = myring + (y & (kRing - 1)) * T::NCT;
-            if (!mbar_wait_warp(&full[ys >> 2], (y / T::RS) & 1, limit, a.err)) return;
+            if (!mbar_wait_warp(&full[ys >> 2], ph, limit, a.err)) return;
 #pragma unroll
             for (int j = 0; j < R; ++j) hsum(left, ys + j, vget<4>(am, j), c[j]);
             mbar_arrive(&empty[ys >> 2]);
@@ -467,20 +477,20 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 push(sb, j, c[j]);
                 kk[j] = vkey(y + j - wy, vget<4>(am, j));
             }
-            atomics(y, kk);
+            atomics(std::true_type{}, y, kk);
             am = an;
+            next_slots();
         }
         // the last input rows and the output rows that lag them
         for (; y < rows; y += R) {
             const uint4 an = __ldg(armq + min((y >> 2) + 1, nquad - 1) * X);
             uint32_t c[R][T::DPT], kk[R];
-            const int ys = y % T::RS;
             Vec *const sb = myring + (y & (kRing - 1)) * T::NCT;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 const int r = y + j;
                 if (r < Y) {
-                    if (j == 0 && !mbar_wait_warp(&full[ys >> 2], (r / T::RS) & 1, limit, a.err))
+                    if (j == 0 && !mbar_wait_warp(&full[ys >> 2], ph, limit, a.err))
                         return;
                     hsum(left, ys + j, vget<4>(am, j), c[j]);
                     if (j == R - 1 || r + 1 == Y) mbar_arrive(&empty[ys >> 2]);
@@ -488,8 +498,9 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
                 }
                 kk[j] = vkey(r - wy, vget<4>(am, j));
             }
-            atomics(y, kk);
+            atomics(std::false_type{}, y, kk);
             am = an;
+            next_slots();
         }
     };
     // warps whose columns are all of the left base take the paired loads
