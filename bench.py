@@ -694,9 +694,9 @@ def main():
                     help="comma-separated forms to measure after the pipeline (batch, serve, diff)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the served request stream")
     ap.add_argument("--tile", type=int, default=-1, help="force a tile shape of the fused kernel (-1: automatic)")
-    ap.add_argument("--lanes", type=int, default=2,
-                    help="library contexts (each on its own stream) that take frames in turn; with more than two "
-                         "the fused kernel's event time in the timed loop includes waiting for the SMs")
+    ap.add_argument("--lanes", type=int, default=6,
+                    help="library contexts (each on its own stream) that take frames in turn, so the small "
+                         "kernels of some frames run while another frame's fused kernel finishes")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the timings of the Table I arm-cap grid, other frame shapes and Dmax (about 20 s)")
     args = ap.parse_args()
