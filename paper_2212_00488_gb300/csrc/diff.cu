@@ -277,35 +277,84 @@ __global__ void __launch_bounds__(kDiffNT) diff_vT_kernel(const float *__restric
     }
 }
 
-// Backward 3: adjoint of the horizontal sum, gathered: G2(x', y) collects the
-// pixels (x, y) whose own window [x - left, x + right] contains x'.
-__global__ void diff_hT_kernel(const float *__restrict__ g1, const uint32_t *__restrict__ arm, int X, int Y,
-                               int wx, int dc, float *__restrict__ g2)
+// Backward 3: adjoint of the horizontal sum. G2(x', y) collects the pixels
+// (x, y) whose own window [x - left, x + right] contains x'. A block takes one
+// row segment of up to kHSeg columns of one pair: it stages the chunk's
+// disparity planes and the arm words of the segment and its wx-column halo in
+// shared memory (coalesced loads), then, as in the vertical adjoint, a thread
+// owns one disparity and a band of 32 columns: each pixel whose window reaches
+// the band adds its value where the window enters and subtracts it one column
+// past where it ends (pixels in ascending x), and a running sum gives the
+// band. The staged rows skip a word every 32, so the 32 bands of a warp,
+// 32 columns apart, read distinct banks. The outputs go back through shared
+// memory and leave in coalesced rows.
+constexpr int kHSeg = 1024;                       // 32 bands of 32 columns
+__host__ __device__ __forceinline__ int hpad(int i) { return i + (i >> 5); }
+
+size_t diff_hT_smem(int X, int wx)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= X * Y) return;
-    const size_t b = blockIdx.y, n = (size_t)X * Y;   // pair
-    g1 += b * kDC * n;
-    arm += b * n;
-    g2 += b * kDC * n;
-    const int y = i / X, xp = i - y * X;
-    const int xa = max(xp - wx, 0), xb = min(xp + wx, X - 1);
+    const int seg = min(X, kHSeg), span = seg + 2 * wx;
+    return (size_t)(kDC + 1) * hpad(span + 31) * 4 + (size_t)kDiffNT * 33 * 4;
+}
+
+__global__ void __launch_bounds__(kDiffNT) diff_hT_kernel(const float *__restrict__ g1,
+                                                          const uint32_t *__restrict__ arm, int X, int Y, int wx,
+                                                          int dc, float *__restrict__ g2)
+{
+    extern __shared__ float hsm[];
+    const int seg = min(X, kHSeg), span = seg + 2 * wx, pitch = hpad(span + 31);
+    float *gs = hsm;                                          // [kDC][pitch] staged planes, then outputs
+    uint32_t *as = reinterpret_cast<uint32_t *>(hsm + kDC * pitch);   // [pitch] arm words
+    float *delta = hsm + (kDC + 1) * pitch;                   // [kDiffNT][33]
+    const int y = blockIdx.y, x0 = blockIdx.x * kHSeg;
+    const int xs = x0 - wx;                                   // column of staged index 0
+    const int x1 = min(x0 + kHSeg, X);                        // segment columns [x0, x1)
+    const size_t b = blockIdx.z, n = (size_t)X * Y;           // pair
     const size_t r = (size_t)y * X;
-    // as in diff_vT_kernel: arms once per pixel, ascending x per disparity
-    float s[kDC];
+    g1 += b * kDC * n;
+    g2 += b * kDC * n;
+    arm += b * n;
+    // stage the planes and arms of columns [max(xs, 0), min(x1 + wx, X))
+    const int sa = max(xs, 0), sb = min(x1 + wx, X);
+    for (int x = sa + (int)threadIdx.x; x < sb; x += kDiffNT) {
+        as[hpad(x - xs)] = arm[r + x];
+        for (int k = 0; k < dc; ++k) gs[k * pitch + hpad(x - xs)] = g1[(size_t)k * n + r + x];
+    }
+    __syncthreads();
+    const int k = threadIdx.x / 32, band = threadIdx.x % 32;
+    const int bx0 = x0 + 32 * band;                           // band columns [bx0, be)
+    const int be = min(bx0 + 32, x1);
+    float *dl = delta + threadIdx.x * 33;
+    float acc[32];
+    const bool work = k < dc && bx0 < be;
+    if (work) {
 #pragma unroll
-    for (int k = 0; k < kDC; ++k) s[k] = 0.f;
-    for (int x = xa; x <= xb; ++x) {
-        const uint32_t am = arm[r + x];
-        if (x - (int)(am & 0xFF) <= xp && xp <= x + (int)((am >> 8) & 0xFF)) {
+        for (int i = 0; i <= 32; ++i) dl[i] = 0.f;
+        const float *gk = gs + k * pitch;
+        const int xa = max(bx0 - wx, 0), xb = min(be - 1 + wx, X - 1);
+        for (int x = xa; x <= xb; ++x) {
+            const uint32_t am = as[hpad(x - xs)];
+            const int lo = x - (int)(am & 0xFF), hi = x + (int)((am >> 8) & 0xFF);
+            if (hi < bx0 || lo >= be) continue;
+            const float v = gk[hpad(x - xs)];
+            dl[max(lo, bx0) - bx0] += v;
+            if (hi + 1 < be) dl[hi + 1 - bx0] -= v;
+        }
+        float sacc = 0.f;
 #pragma unroll
-            for (int k = 0; k < kDC; ++k)
-                if (k < dc) s[k] += g1[(size_t)k * X * Y + r + x];
+        for (int i = 0; i < 32; ++i) {
+            sacc += dl[i];
+            acc[i] = sacc;
         }
     }
+    __syncthreads();                              // every thread is done with the staged planes
+    if (work)
 #pragma unroll
-    for (int k = 0; k < kDC; ++k)
-        if (k < dc) g2[(size_t)k * X * Y + i] = s[k];
+        for (int i = 0; i < 32; ++i)
+            if (bx0 + i < be) gs[k * pitch + hpad(bx0 + i - xs)] = acc[i];
+    __syncthreads();
+    for (int x = x0 + (int)threadIdx.x; x < x1; x += kDiffNT)
+        for (int kk = 0; kk < dc; ++kk) g2[(size_t)kk * n + r + x] = gs[kk * pitch + hpad(x - xs)];
 }
 
 // Backward 4: through the cost. Per pixel: its own gradient as the left pixel
@@ -496,9 +545,14 @@ size_t diff_workspace_bytes(int X, int Y, int wy, int B, int D)
 
 cudaError_t diff_setup()
 {
-    // the cost rows of a chunk take up to kDC * 4096 floats of shared memory
-    return cudaFuncSetAttribute(diff_costx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kDC * 4096 * (int)sizeof(float));
+    // the cost rows of a chunk take up to kDC * 4096 floats of shared memory;
+    // the horizontal adjoint stages a 1024-column segment with a halo of up to
+    // 141 columns each side
+    cudaError_t e = cudaFuncSetAttribute(diff_costx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kDC * 4096 * (int)sizeof(float));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(diff_hT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)diff_hT_smem(kHSeg, kMaxWx));
 }
 
 cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
@@ -543,7 +597,8 @@ cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
                                                               a.dhat, a.stats, a.grad_dhat, w.s1);
             diff_vT_kernel<<<dim3((X + 31) / 32, (Y + kVB - 1) / kVB, B), kDiffNT, 0, s>>>(w.s1, w.arml, X, Y,
                                                                                       a.wy, dc, w.s2);
-            diff_hT_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.s2, w.arml, X, Y, a.wx, dc, w.s3);
+            diff_hT_kernel<<<dim3((X + kHSeg - 1) / kHSeg, Y, B), kDiffNT, diff_hT_smem(X, a.wx), s>>>(
+                w.s2, w.arml, X, Y, a.wx, dc, w.s3);
             diff_costgrad_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.gl, w.gr, w.pixl, w.pixr, a.theta, X, Y, a.D,
                                                                    d0, dc, w.s3, w.accl, w.accr,
                                                                    w.part + (size_t)c * nblk * 4, part_pair);
