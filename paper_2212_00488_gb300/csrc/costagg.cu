@@ -218,10 +218,20 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
             if (y >= Y) return;
             const uint32_t *pl = a.pix_l + (size_t)y * X;
             const uint32_t *pr = a.pix_r + (size_t)y * X;
+            if (all_in) {
+                // every entry and match lies in the image: one base per row,
+                // the entries at fixed offsets from it
+                const uint32_t *bl = pl + xb, *br = pr + (xb - d0 - (T::DS - 1));
 #pragma unroll
-            for (int k = 0; k < T::KE; ++k) pv[k] = __ldg(pl + offl[k]);
+                for (int k = 0; k < T::KE; ++k) pv[k] = __ldg(bl + k);
 #pragma unroll
-            for (int k = 0; k < T::KE + T::DS - 1; ++k) qv[k] = __ldg(pr + offr[k]);
+                for (int k = 0; k < T::KE + T::DS - 1; ++k) qv[k] = __ldg(br + k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < T::KE; ++k) pv[k] = __ldg(pl + offl[k]);
+#pragma unroll
+                for (int k = 0; k < T::KE + T::DS - 1; ++k) qv[k] = __ldg(pr + offr[k]);
+            }
         };
         // The next row's pixels are loaded into the same registers as soon
         // as this row's costs are formed, and the wait for a free slot comes
@@ -233,7 +243,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
         auto cost = [&](auto border, int k, int q) -> uint32_t {
             constexpr bool kBorder = decltype(border)::value;
             const uint32_t pk = pv0[k], qk = qv0[k + T::DS - 1 - q];
-            const uint32_t ad = (uint32_t)abs((int)(pk & 0xFF) - (int)(qk & 0xFF));
+            const uint32_t ad = __vabsdiffu4(pk, qk) & 0xFFu;     // |grey difference| from the low bytes
             uint32_t v = lut[__popc((pk ^ qk) & 0x3F00u) * kLutPitch + ad];
             if (kBorder) v = (inimg >> (k * T::DS + q)) & 1u ? v : P;
             return v;
