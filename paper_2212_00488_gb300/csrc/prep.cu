@@ -73,86 +73,72 @@ __global__ void downscale_kernel(const uint8_t *__restrict__ g_l, const uint8_t 
 }
 
 // Grey conversion and Eq. 2 downscale in one pass (the downscaling path, for
-// W a multiple of 4 and 4-byte aligned RGB rows). A CTA makes a kGDX x kGDY
-// tile of downscaled pixels of one image: it converts the full-res pixels
-// [2 x0 - 4, 2 x0 + 2 kGDX + 4) of rows 2 y0 - 1 .. 2 y0 + 2 kGDY - 1 (row and
-// column coordinates clamped, as in downscale_kernel) four at a time from
-// three aligned words, keeps them in shared memory, writes the left image's
-// full-res grey of its interior (the scale-up reads it) and the 3x3 means.
-// Same arithmetic as grey_kernel followed by downscale_kernel.
-constexpr int kGDX = 64, kGDY = 4;
-constexpr int kGRW = 2 * kGDX + 8, kGRH = 2 * kGDY + 1;   // region: 136 x 9 pixels
+// W a multiple of 4 and 4-byte aligned RGB rows). Thread (band, c) of one
+// image owns full-res columns 4c .. 4c + 3 and makes the 3x3 means of output
+// columns 2c, 2c + 1, rows 4 band .. 4 band + 3. It converts rows
+// 8 band - 1 .. 8 band + 7 of its columns (row coordinates clamped, as in
+// downscale_kernel), each from three aligned words, all requested before the
+// first is used; the grey of pixel 4c - 1 comes from the word its left
+// neighbour loaded (a shuffle; lane 0 loads it itself). Grey values stay in
+// registers; the left image's full-res grey of rows 8 band .. 8 band + 7 is
+// written for the scale-up. Bands cover ceil(H / 2) rows so that the last row
+// of an odd H gets its grey. Same arithmetic as grey_kernel followed by
+// downscale_kernel.
+constexpr int kGDT = 128;                  // threads per CTA
+constexpr int kGDB = 4;                    // output rows per thread
+constexpr int kGDR = 2 * kGDB + 1;         // full-res rows per thread
 
-__global__ void __launch_bounds__(kGDX * kGDY) grey_down_kernel(
+__global__ void __launch_bounds__(kGDT) grey_down_kernel(
     const uint8_t *__restrict__ rgb_l, const uint8_t *__restrict__ rgb_r, uint8_t *__restrict__ gf_l,
-    uint8_t *__restrict__ s_l, uint8_t *__restrict__ s_r, int W, int H)
+    uint8_t *__restrict__ s_l, uint8_t *__restrict__ s_r, int W, int H, int ncol, int nband)
 {
-    __shared__ __align__(4) uint8_t reg[kGRH][kGRW];
     pdl_trigger();
-    const bool right = blockIdx.z != 0;
+    const bool right = blockIdx.y != 0;
+    const int t0 = blockIdx.x * kGDT + threadIdx.x;
+    const int nthr = ncol * nband;
+    // threads past the end take the last thread's pixels for the shuffles
+    // and store nothing
+    const bool live = t0 < nthr;
+    const int t = live ? t0 : nthr - 1;
+    const int band = t / ncol, c = t - band * ncol;   // left neighbour (band, c - 1) is thread t - 1
+    const int lane = threadIdx.x & 31;
     const uint8_t *rgb = right ? rgb_r : rgb_l;
     uint8_t *s = right ? s_r : s_l;
     const int X = W / 2, Y = H / 2;
-    const int x0 = blockIdx.x * kGDX, y0 = blockIdx.y * kGDY;
-    const int fx0 = 2 * x0 - 4, fy0 = 2 * y0 - 1;     // full-res origin of the region
-    constexpr int kGroups = kGRW / 4, kN = kGroups * kGRH, kNT = kGDX * kGDY;
-    constexpr int kPer = (kN + kNT - 1) / kNT;                 // groups per thread
-    // all loads of the thread first, so that they are in flight together
-    uint32_t w[kPer][3];
-    bool inside[kPer];
+    uint32_t w[kGDR][3], wh[kGDR];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int i = threadIdx.x + k * kNT;
-        const int gx = i % kGroups, ry = i / kGroups;
-        const int fx = fx0 + 4 * gx;
-        inside[k] = i < kN && fx >= 0 && fx + 4 <= W;
-        if (inside[k]) {
-            const uint32_t *p = reinterpret_cast<const uint32_t *>(
-                rgb + ((size_t)min(max(fy0 + ry, 0), H - 1) * W + fx) * 3);
-            w[k][0] = __ldg(p);
-            w[k][1] = __ldg(p + 1);
-            w[k][2] = __ldg(p + 2);
-        }
-    }
+    for (int r = 0; r < kGDR; ++r) {
+        const int fy = min(max(8 * band - 1 + r, 0), H - 1);
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(rgb + ((size_t)fy * W + 4 * c) * 3);
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int i = threadIdx.x + k * kNT;
-        if (i >= kN) break;
-        const int gx = i % kGroups, ry = i / kGroups;
-        const int fx = fx0 + 4 * gx, fy = fy0 + ry;
-        uint32_t q;
-        if (inside[k]) {
-            q = luma4(w[k][0], w[k][1], w[k][2]);
-        } else {
-            // a group across the left or right border: clamped pixel by pixel
-            const uint8_t *row = rgb + (size_t)min(max(fy, 0), H - 1) * 3 * W;
-            q = 0;
-            for (int c = 0; c < 4; ++c) {
-                const uint8_t *p = row + 3 * min(max(fx + c, 0), W - 1);
-                q |= luma(__ldg(p), __ldg(p + 1), __ldg(p + 2)) << (8 * c);
-            }
-        }
-        *reinterpret_cast<uint32_t *>(&reg[ry][4 * gx]) = q;
-        // interior: columns [2 x0, 2 x0 + 2 kGDX), rows [2 y0, 2 y0 + 2 kGDY)
-        if (!right && gx >= 1 && gx <= 2 * kGDX / 4 && ry >= 1 && fx < W && fy < H)
-            *reinterpret_cast<uint32_t *>(gf_l + (size_t)fy * W + fx) = q;
+        for (int i = 0; i < 3; ++i) w[r][i] = __ldg(p + i);
+        wh[r] = lane == 0 && c > 0 ? __ldg(p - 1) : 0u;
     }
-    __syncthreads();
-    const int lx = threadIdx.x % kGDX, ly = threadIdx.x / kGDX;
-    const int x = x0 + lx, y = y0 + ly;
-    if (x >= X || y >= Y) return;
-    // the window's three bytes of a row start at byte 2 lx + 3 (1 or 3 mod 4):
-    // byte sums of the two words that hold them, as dot products with 0/1 masks
-    const int b0 = 2 * lx + 3, wa = b0 >> 2;
-    const uint32_t m0 = (b0 & 3) == 1 ? 0x01010100u : 0x01000000u;
-    const uint32_t m1 = (b0 & 3) == 1 ? 0u : 0x00000101u;
-    uint32_t sum = 0;
+    // horizontal 3-sums of row r at full-res columns 4c and 4c + 2
+    uint32_t hs[kGDR][2];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const uint32_t *rw = reinterpret_cast<const uint32_t *>(reg[2 * ly + j]);
-        sum = __dp4a(rw[wa], m0, __dp4a(rw[wa + 1], m1, sum));
+    for (int r = 0; r < kGDR; ++r) {
+        // the word before this thread's first: pixel 4c - 1 in bytes 1..3
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, w[r][2], 1);
+        const uint32_t hw = lane == 0 ? wh[r] : prev;
+        const uint32_t g = luma4(w[r][0], w[r][1], w[r][2]);
+        // pixel 4c - 1, or pixel 0 (clamped) for the first column group
+        const uint32_t gh = c > 0 ? __dp4a(hw, kLumaW << 8, 128u) >> 8 : (g & 0xFFu);
+        hs[r][0] = __dp4a(g, 0x00000101u, gh);
+        hs[r][1] = __dp4a(g, 0x01010100u, 0u);
+        const int fy = 8 * band - 1 + r;
+        if (live && !right && r > 0 && fy < H) *reinterpret_cast<uint32_t *>(gf_l + (size_t)fy * W + 4 * c) = g;
     }
-    s[(size_t)y * X + x] = (uint8_t)((sum + 4) / 9);
+    if (!live) return;
+#pragma unroll
+    for (int i = 0; i < kGDB; ++i) {
+        const int y = kGDB * band + i;
+        if (y >= Y) break;
+        const uint32_t m0 = (hs[2 * i][0] + hs[2 * i + 1][0] + hs[2 * i + 2][0] + 4u) / 9u;
+        const uint32_t m1 = (hs[2 * i][1] + hs[2 * i + 1][1] + hs[2 * i + 2][1] + 4u) / 9u;
+        // X is even: output pixel 2c starts a 2-byte aligned pair
+        *reinterpret_cast<uint16_t *>(s + (size_t)y * X + 2 * c) = (uint16_t)(m0 | m1 << 8);
+    }
 }
 
 // Support data in two passes, each with a halo only along its own axis.
@@ -490,9 +476,11 @@ cudaError_t launch_grey_down(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t
         cudaError_t e = launch_grey(rgb_l, rgb_r, gf_l, gf_r, W, H, s);
         return e != cudaSuccess ? e : launch_downscale(gf_l, gf_r, s_l, s_r, W, H, s);
     }
-    // W a multiple of 4: every interior group of four lies inside the row
-    dim3 grid((X + kGDX - 1) / kGDX, ((H + 1) / 2 + kGDY - 1) / kGDY, 2);
-    grey_down_kernel<<<grid, kGDX * kGDY, 0, s>>>(rgb_l, rgb_r, gf_l, s_l, s_r, W, H);
+    // W a multiple of 4: a thread's group of four lies inside the row
+    const int ncol = W / 4, nband = ((H + 1) / 2 + kGDB - 1) / kGDB;
+    const long nthr = (long)ncol * nband;
+    dim3 grid((unsigned)((nthr + kGDT - 1) / kGDT), 2);
+    grey_down_kernel<<<grid, kGDT, 0, s>>>(rgb_l, rgb_r, gf_l, s_l, s_r, W, H, ncol, nband);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -133,6 +133,8 @@ def test_full_vertical_arms_every_tile(tile):
     (5, 4, 9, 1),        # downscaled to 2 x 2
     (257, 129, 64, 1),   # odd full-res size
     (600, 90, 300, 1),   # D = 150 after halving, wider than many strips
+    (268, 67, 20, 1),    # fused grey + downscale: W = 8k + 4, odd H (last row's grey)
+    (16, 3, 5, 1),       # fused grey + downscale: one output row, odd H
 ])
 def test_edge_shapes(W, H, dmax, ds):
     s = scenes.make_scene(W, H, dmax, planes=3, seed=W * 7 + H)
