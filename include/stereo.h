@@ -51,8 +51,9 @@ enum {
     STEREO_STAGE_SCALEDOWN = 0, /* grey + mean-pool downscale (SD) */
     STEREO_STAGE_SUPPORT = 1,   /* mini-census codes and the four cross arms (W+-, W*+-) */
     STEREO_STAGE_COSTAGG = 2,   /* fused cost + x/y aggregation + WTA, both bases (C+CA_x, CA) */
-    STEREO_STAGE_REFINE = 3,    /* cross-check + median + bilateral fill (CC, Post) */
-    STEREO_STAGE_UPSCALE = 4,   /* scale-up (SU) */
+    STEREO_STAGE_REFINE = 3,    /* cross-check + median + bilateral fill (CC, Post), and with
+                                   downscaling the scale-up (SU) in the same kernel */
+    STEREO_STAGE_UPSCALE = 4,   /* scale-up (SU): part of stage 3; launches nothing, reports 0 */
     STEREO_NUM_STAGES = 5
 };
 

@@ -25,7 +25,7 @@ STAGE_COSTAGG = 2
 STAGE_REFINE = 3
 STAGE_UPSCALE = 4
 NUM_STAGES = 5
-STAGE_NAMES = ["SD", "W+-/W*+-", "C+CA_x+CA", "CC+Post", "SU"]
+STAGE_NAMES = ["SD", "W+-/W*+-", "C+CA_x+CA", "CC+Post+SU", "SU"]
 
 
 class stereo_job(ctypes.Structure):

@@ -382,7 +382,7 @@ __device__ __forceinline__ void costagg_tile(const CostAggArgs &a, const int x0,
     // columns read disparity k at column + k, so each half on its own. A byte
     // permutation takes a 16-bit difference and places it at bits 8..23.
     auto hsum = [&](auto left, int slot, uint32_t am, uint32_t (&cax)[T::DPT]) {
-        constexpr bool kLeft = decltype(left)::value;
+        [[maybe_unused]] constexpr bool kLeft = decltype(left)::value;
         const int hi = ((am >> 8) & 0xFF) + 1, lo = am & 0xFF;
         if constexpr (T::S16) {
             const uint32_t *w = wrow0 + slot * (2 * T::SWP);

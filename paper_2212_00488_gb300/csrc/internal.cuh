@@ -135,8 +135,11 @@ cudaError_t launch_costagg(const CostAggArgs &a, cudaStream_t s);
 cudaError_t launch_refine(const uint32_t *key_l, const uint32_t *key_r, const uint8_t *grey_l,
                           int X, int Y, int T, int fill_mode, uint8_t *dl, uint8_t *dr, uint8_t *gcp,
                           uint8_t *dm, float *dplus, cudaStream_t s);
-cudaError_t launch_upscale(const float *dplus, const uint8_t *grey_low, const uint8_t *grey_full,
-                           int X, int Y, int W, int H, int T, float *out, cudaStream_t s);
+// The downscaling path's Steps 6-8 in one kernel: the maps and dplus of
+// launch_refine, and the full-resolution disparity in out.
+cudaError_t launch_refine_up(const uint32_t *key_l, const uint32_t *key_r, const uint8_t *grey_low,
+                             const uint8_t *grey_full, int X, int Y, int W, int H, int T, int fill_mode, uint8_t *dl,
+                             uint8_t *dr, uint8_t *gcp, uint8_t *dm, float *dplus, float *out, cudaStream_t s);
 cudaError_t launch_unpack_planes(const uint32_t *pix, const uint32_t *arm, uint8_t *grey,
                                  uint8_t *census, uint32_t *arms, int X, int Y, cudaStream_t s);
 

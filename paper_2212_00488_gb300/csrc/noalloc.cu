@@ -150,10 +150,11 @@ extern "C" int stereo_compute_noalloc(const stereo_params *params, const uint8_t
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         a.num_sms = nsm;
-        if ((e = launch_costagg(a, s)) == cudaSuccess &&
-            (e = launch_refine(u32(o_key[0]), u32(o_key[1]), u8(o_gs[0]), X, Y, p.t_fill, p.fill_mode, dl_out, dr_out, gcp_out,
-                               u8(o_dm), dplus, s)) == cudaSuccess && ds)
-            e = launch_upscale(dplus, u8(o_gs[0]), u8(o_gf[0]), X, Y, W, H, p.t_fill, disp_out, s);
+        if ((e = launch_costagg(a, s)) == cudaSuccess)
+            e = ds ? launch_refine_up(u32(o_key[0]), u32(o_key[1]), u8(o_gs[0]), u8(o_gf[0]), X, Y, W, H, p.t_fill,
+                                      p.fill_mode, dl_out, dr_out, gcp_out, u8(o_dm), dplus, disp_out, s)
+                   : launch_refine(u32(o_key[0]), u32(o_key[1]), u8(o_gs[0]), X, Y, p.t_fill, p.fill_mode, dl_out, dr_out,
+                                   gcp_out, u8(o_dm), dplus, s);
     }
     if (e != cudaSuccess) return say(err, err_len, STEREO_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     return STEREO_OK;

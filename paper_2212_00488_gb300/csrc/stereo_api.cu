@@ -282,12 +282,13 @@ cudaError_t run_stage(stereo_ctx *c, int stage, cudaStream_t s)
     }
     case STEREO_STAGE_REFINE:
         c->launches++;
+        if (ds)   // the scale-up runs in the same kernel
+            return launch_refine_up(c->key[0], c->key[1], c->gs[0], c->gf[0], c->X, c->Y, c->W, c->H, c->p.t_fill,
+                                    c->p.fill_mode, c->out_dl, c->out_dr, c->out_gcp, c->dm, c->dplus, c->out_disp, s);
         return launch_refine(c->key[0], c->key[1], c->gs[0], c->X, c->Y, c->p.t_fill, c->p.fill_mode, c->out_dl, c->out_dr,
                              c->out_gcp, c->dm, c->dplus, s);
     case STEREO_STAGE_UPSCALE:
-        if (!ds) return cudaSuccess;
-        c->launches++;
-        return launch_upscale(c->dplus, c->gs[0], c->gf[0], c->X, c->Y, c->W, c->H, c->p.t_fill, c->out_disp, s);
+        return cudaSuccess;   // inside the refine stage's kernel (downscaling) or nothing to do
     default:
         return cudaErrorInvalidValue;
     }
@@ -323,7 +324,7 @@ int run_frame(stereo_ctx *c, cudaStream_t s)
         if (sl) cudaEventRecord(sl->ev[st], s);
         cudaError_t e = run_stage(c, st, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
-        if (sl) sl->ran[st] = c->p.downscale || st != STEREO_STAGE_UPSCALE;
+        if (sl) sl->ran[st] = st != STEREO_STAGE_UPSCALE;
     }
     if (sl) {
         cudaEventRecord(sl->ev[STEREO_NUM_STAGES], s);
@@ -707,15 +708,12 @@ cudaError_t batch_prep(stereo_ctx *c, const stereo_job &j, const FrameWs &f, cud
 
 cudaError_t batch_post(stereo_ctx *c, const stereo_job &j, const FrameWs &f, cudaStream_t s, int &launches)
 {
-    float *dplus = c->p.downscale ? f.dplus : j.disp_out;
-    cudaError_t e = launch_refine(f.key[0], f.key[1], f.gs[0], f.X, f.Y, c->p.t_fill, c->p.fill_mode, j.dl_out, j.dr_out,
-                                  j.gcp_out, f.dm, dplus, s);
     launches++;
-    if (e == cudaSuccess && c->p.downscale) {
-        e = launch_upscale(dplus, f.gs[0], f.gf[0], f.X, f.Y, f.W, f.H, c->p.t_fill, j.disp_out, s);
-        launches++;
-    }
-    return e;
+    if (c->p.downscale)
+        return launch_refine_up(f.key[0], f.key[1], f.gs[0], f.gf[0], f.X, f.Y, f.W, f.H, c->p.t_fill, c->p.fill_mode,
+                                j.dl_out, j.dr_out, j.gcp_out, f.dm, f.dplus, j.disp_out, s);
+    return launch_refine(f.key[0], f.key[1], f.gs[0], f.X, f.Y, c->p.t_fill, c->p.fill_mode, j.dl_out, j.dr_out,
+                         j.gcp_out, f.dm, j.disp_out, s);
 }
 
 std::string batch_signature(const stereo_ctx *c, const std::vector<FrameWs> &fw)

@@ -264,7 +264,8 @@ def test_stage_relaunch_and_profiling():
     ms, nframes = _lib.stereo_stage_ms(st.ctx)
     assert nframes == 1
     assert len(ms) == 5 and all(t >= 0 for t in ms) and ms[_lib.STAGE_COSTAGG] > 0
-    assert _lib.stereo_last_launch_count(st.ctx) == 5
+    # grey + downscale, support, fused cost/aggregation/WTA, refine + scale-up
+    assert _lib.stereo_last_launch_count(st.ctx) == 4 and ms[_lib.STAGE_UPSCALE] == 0
     first = out.dl.clone()
     for stage in range(_lib.NUM_STAGES):
         _lib.stereo_launch_stage(st.ctx, stage, stream_handle(torch.cuda.current_stream()))
