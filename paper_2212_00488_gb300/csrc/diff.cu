@@ -15,10 +15,11 @@
 // chunks of kDC, keeping per chunk the x-aggregated slab and, in backward,
 // the slab's gradients. Every pair of the batch has its own buffers, and the
 // per-chunk kernels take all pairs in one launch (blockIdx.y = pair), so a
-// launch is several waves of blocks rather than one and a partial one. Sums over arms are direct (at most 2 wx + 1 and
-// 2 wy + 1 terms), which keeps FP32 aggregates within about 6e-6 of their
-// exact value. The adjoint gathers for every cell the anchors whose support
-// contains it, so no float atomics are used and results are deterministic.
+// launch is several waves of blocks rather than one and a partial one. Sums
+// over arms are direct (at most 2 wx + 1 and 2 wy + 1 terms), which keeps FP32
+// aggregates within about 6e-6 of their exact value. The adjoint of each sum
+// is a banded difference array walked in a fixed order by one thread, so no
+// float atomics are used and results are deterministic.
 #include "internal.cuh"
 
 namespace stereo {
@@ -95,18 +96,27 @@ __global__ void diff_costx_kernel(const float *__restrict__ gL, const float *__r
     const float P = th.wad * (1.f - expf(-1.f / th.lad)) + th.wmc * (1.f - expf(-6.f / th.lmc));
     const size_t r = (size_t)y * X;
     const int kn = min(dc, D - d0);
+    // the census term takes seven values: one exp per Hamming distance
+    __shared__ float mc[8];
+    if (threadIdx.x < 7) mc[threadIdx.x] = th.wmc * (1.f - expf(-(float)threadIdx.x / th.lmc));
+    const float inv_lad = 1.f / th.lad;
+    __syncthreads();
     for (int x = threadIdx.x; x < X; x += blockDim.x) {
         const float gl = gL[r + x];
         const uint32_t pl = pixL[r + x];
-        for (int k = 0; k < kn; ++k) {
-            const int d = d0 + k;
-            float c = P;
-            if (x >= d) {
-                const float a = fabsf(gl - gR[r + x - d]);
-                const int h = __popc((pl ^ pixR[r + x - d]) & 0x3F00u);
-                c = th.wad * (1.f - expf(-a / th.lad)) + th.wmc * (1.f - expf(-(float)h / th.lmc));
+        // the chunk's disparities unrolled, so their loads and exps overlap
+#pragma unroll
+        for (int k = 0; k < kDC; ++k) {
+            if (k < kn) {
+                const int d = d0 + k;
+                float c = P;
+                if (x >= d) {
+                    const float a = fabsf(gl - gR[r + x - d]);
+                    const int h = __popc((pl ^ pixR[r + x - d]) & 0x3F00u);
+                    c = th.wad * (1.f - expf(-a * inv_lad)) + mc[h];
+                }
+                crow[k * X + x] = c;
             }
-            crow[k * X + x] = c;
         }
     }
     __syncthreads();
@@ -378,39 +388,55 @@ __global__ void diff_costgrad_kernel(const float *__restrict__ gL, const float *
     acc_r += b * n;
     part += b * part_pair;
     const Theta th = load_theta(theta);
+    const float inv_lad = 1.f / th.lad, inv_lmc = 1.f / th.lmc;
+    const float kad = th.wad * inv_lad;                 // w_AD / l_AD
+    const float dad = th.wad * inv_lad * inv_lad;       // w_AD / l_AD^2
+    const float dmc = th.wmc * inv_lmc * inv_lmc;       // w_MC / l_MC^2
+    // exp(-h / l_MC) for the seven Hamming distances
+    __shared__ float eh_t[8];
+    if (threadIdx.x < 7) eh_t[threadIdx.x] = expf(-(float)threadIdx.x * inv_lmc);
+    __syncthreads();
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
     if (i < X * Y) {
         const int y = i / X, x = i - y * X;
         const size_t r = (size_t)y * X;
+        const int kn = min(dc, D - d0);
+        const float gl = gL[i], gr = gR[i];
+        const uint32_t pl = pixL[i];
+        const float ea1 = expf(-inv_lad), eh6 = eh_t[6];   // the terms of P (|a| = 1, h = 6)
         float al = 0.f, ar = 0.f;
-        for (int k = 0; k < dc && d0 + k < D; ++k) {
-            const int d = d0 + k;
-            const float *plane = g2 + (size_t)k * X * Y;
-            const float g = plane[i];
-            if (x < d) {
-                const float ea = expf(-1.f / th.lad), eh = expf(-6.f / th.lmc);
-                t0 += g * (1.f - ea);
-                t1 += g * (1.f - eh);
-                t2 += g * th.wad * (-ea / (th.lad * th.lad));
-                t3 += g * th.wmc * (-eh * 6.f / (th.lmc * th.lmc));
-            } else {
-                const float diff = gL[i] - gR[i - d], a = fabsf(diff);
-                const float h = (float)__popc((pixL[i] ^ pixR[i - d]) & 0x3F00u);
-                const float ea = expf(-a / th.lad), eh = expf(-h / th.lmc);
-                t0 += g * (1.f - ea);
-                t1 += g * (1.f - eh);
-                t2 += g * th.wad * (-ea * a / (th.lad * th.lad));
-                t3 += g * th.wmc * (-eh * h / (th.lmc * th.lmc));
-                const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-                al += g * th.wad * ea / th.lad * sgn;
-            }
-            // this pixel as the match of the left pixel x + d
-            if (x + d < X) {
-                const float gg = plane[r + x + d];
-                const float diff = gL[r + x + d] - gR[i], a = fabsf(diff);
-                const float ea = expf(-a / th.lad);
-                const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-                ar -= gg * th.wad * ea / th.lad * sgn;
+        // the chunk's disparities unrolled, so their loads and exps overlap
+#pragma unroll
+        for (int k = 0; k < kDC; ++k) {
+            if (k < kn) {
+                const int d = d0 + k;
+                const float *plane = g2 + (size_t)k * X * Y;
+                const float g = plane[i];
+                if (x < d) {
+                    t0 += g * (1.f - ea1);
+                    t1 += g * (1.f - eh6);
+                    t2 += g * (-ea1 * dad);
+                    t3 += g * (-eh6 * 6.f * dmc);
+                } else {
+                    const float diff = gl - gR[i - d], a = fabsf(diff);
+                    const int hi = __popc((pl ^ pixR[i - d]) & 0x3F00u);
+                    const float h = (float)hi;
+                    const float ea = expf(-a * inv_lad), eh = eh_t[hi];
+                    t0 += g * (1.f - ea);
+                    t1 += g * (1.f - eh);
+                    t2 += g * (-ea * a * dad);
+                    t3 += g * (-eh * h * dmc);
+                    const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+                    al += g * kad * ea * sgn;
+                }
+                // this pixel as the match of the left pixel x + d
+                if (x + d < X) {
+                    const float gg = plane[r + x + d];
+                    const float diff = gL[r + x + d] - gr, a = fabsf(diff);
+                    const float ea = expf(-a * inv_lad);
+                    const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+                    ar -= gg * kad * ea * sgn;
+                }
             }
         }
         acc_l[i] += al;
