@@ -483,24 +483,18 @@ __global__ void diff_finish_kernel(const float *__restrict__ acc_l, const float 
     }
 }
 
-// Sum of all block partials in a fixed order (double accumulation): thread t
-// adds partials t, t + kRedNT, ... in turn, then a fixed pairwise tree adds
-// the threads' sums, so the result does not depend on scheduling.
-constexpr int kRedNT = 1024;
+// Sum of all block partials in a fixed order (double accumulation), in two
+// levels so that the FP64 adds spread over the GPU. Level 1: block j sums the
+// contiguous segment j of the partials (thread t takes its elements t, t +
+// kRedNT, ... in turn, then a fixed pairwise tree adds the threads' sums).
+// Level 2: one block adds the kRedBlocks segment sums by the same fixed tree.
+// Neither order depends on scheduling.
+constexpr int kRedNT = 256;
+constexpr int kRedBlocks = 128;
 
-__global__ void __launch_bounds__(kRedNT) diff_theta_reduce_kernel(const float *__restrict__ part, int nparts,
-                                                                   float *__restrict__ grad)
+__device__ __forceinline__ void tree_sum4(double (*sh)[kRedNT], double s0, double s1, double s2, double s3)
 {
-    __shared__ double sh[4][kRedNT];
     const int t = threadIdx.x;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int k = t; k < nparts; k += kRedNT) {
-        const float4 v = *reinterpret_cast<const float4 *>(part + (size_t)k * 4);
-        s0 += (double)v.x;
-        s1 += (double)v.y;
-        s2 += (double)v.z;
-        s3 += (double)v.w;
-    }
     sh[0][t] = s0;
     sh[1][t] = s1;
     sh[2][t] = s2;
@@ -512,6 +506,34 @@ __global__ void __launch_bounds__(kRedNT) diff_theta_reduce_kernel(const float *
             for (int c = 0; c < 4; ++c) sh[c][t] += sh[c][t + o];
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kRedNT) diff_theta_segments_kernel(const float *__restrict__ part, int nparts,
+                                                                     double *__restrict__ seg)
+{
+    __shared__ double sh[4][kRedNT];
+    const int t = threadIdx.x, len = (nparts + kRedBlocks - 1) / kRedBlocks;
+    const int k0 = min(nparts, (int)blockIdx.x * len), k1 = min(nparts, k0 + len);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int k = k0 + t; k < k1; k += kRedNT) {
+        const float4 v = *reinterpret_cast<const float4 *>(part + (size_t)k * 4);
+        s0 += (double)v.x;
+        s1 += (double)v.y;
+        s2 += (double)v.z;
+        s3 += (double)v.w;
+    }
+    tree_sum4(sh, s0, s1, s2, s3);
+    if (t < 4) seg[blockIdx.x * 4 + t] = sh[t][0];
+}
+
+__global__ void __launch_bounds__(kRedNT) diff_theta_reduce_kernel(const double *__restrict__ seg,
+                                                                   float *__restrict__ grad)
+{
+    static_assert(kRedBlocks <= kRedNT, "one segment sum per thread");
+    __shared__ double sh[4][kRedNT];
+    const int t = threadIdx.x;
+    const bool h = t < kRedBlocks;
+    tree_sum4(sh, h ? seg[t * 4] : 0.0, h ? seg[t * 4 + 1] : 0.0, h ? seg[t * 4 + 2] : 0.0, h ? seg[t * 4 + 3] : 0.0);
     if (t < 4) grad[t] = (float)sh[t][0];
 }
 
@@ -525,6 +547,7 @@ struct DiffWs {
     uint8_t *ql, *qr;
     uint32_t *pixl, *pixr, *arml, *armr, *armcl, *armcr, *keyl, *keyr;
     float *ns, *state, *accl, *accr, *s0, *s1, *s2, *s3, *part;
+    double *seg;
 };
 
 size_t diff_layout(char *base, int X, int Y, int wy, int B, int D, DiffWs *w)
@@ -560,6 +583,7 @@ size_t diff_layout(char *base, int X, int Y, int wy, int B, int D, DiffWs *w)
     t.s2 = (float *)take(nb * kDC * n * 4);
     t.s3 = (float *)take(nb * kDC * n * 4);
     t.part = (float *)take(nb * nchunks * nblk * 16);        // parameter-gradient partials
+    t.seg = (double *)take(kRedBlocks * 4 * sizeof(double)); // their segment sums
     if (w) *w = t;
     return off;
 }
@@ -633,7 +657,8 @@ cudaError_t diff_run(const DiffArgs &a, cudaStream_t s)
     }
     if (a.backward) {
         diff_finish_kernel<<<dim3(nblk, B), kDiffNT, 0, s>>>(w.accl, w.accr, n, a.grad_left, a.grad_right);
-        diff_theta_reduce_kernel<<<1, kRedNT, 0, s>>>(w.part, B * nchunks * nblk, a.grad_theta);
+        diff_theta_segments_kernel<<<kRedBlocks, kRedNT, 0, s>>>(w.part, B * nchunks * nblk, w.seg);
+        diff_theta_reduce_kernel<<<1, kRedNT, 0, s>>>(w.seg, a.grad_theta);
     }
     return cudaGetLastError();
 }
