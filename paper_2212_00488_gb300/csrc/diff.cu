@@ -272,13 +272,15 @@ __global__ void __launch_bounds__(kDiffNT) diff_vT_kernel(const float *__restric
 #pragma unroll
     for (int i = 0; i <= kVB; ++i) dl[i] = 0.f;
     const int ya = max(y0 - wy, 0), yb = min(ye - 1 + wy, Y - 1);
+#pragma unroll 4
     for (int y = ya; y <= yb; ++y) {
         const uint32_t am = arm[(size_t)y * X + x];
+        const float v = gp[(size_t)y * X];           // rows [ya, yb] are in the image: loaded ahead of the test
         const int lo = y - (int)((am >> 16) & 0xFF), hi = y + (int)(am >> 24);
-        if (hi < y0 || lo >= ye) continue;
-        const float v = gp[(size_t)y * X];
-        dl[max(lo, y0) - y0] += v;
-        if (hi + 1 < ye) dl[hi + 1 - y0] -= v;
+        if (hi >= y0 && lo < ye) {
+            dl[max(lo, y0) - y0] += v;
+            if (hi + 1 < ye) dl[hi + 1 - y0] -= v;
+        }
     }
     float s = 0.f;
     for (int i = 0; i < ye - y0; ++i) {
