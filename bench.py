@@ -219,6 +219,15 @@ def cpu_baseline_leg():
     one = rate(2, whole)
     oracle.set_threads(0)
     fp64 = rate(2, lambda: oracle.wta_pair_f64(left, right, DMAX, oracle.Params()))
+    # the small configuration: 360x248, Dmax 36, no downscaling
+    s0 = scenes.make_scene(360, 248, 36, 12, SEED)
+    p0 = oracle.Params()
+    p0.downscale = 0
+    small = lambda: oracle.pipeline(s0.left, s0.right, 36, p0)   # noqa: E731
+    small_all = rate(20, small)
+    oracle.set_threads(1)
+    small_one = rate(5, small)
+    oracle.set_threads(0)
     return {"value": all_cores, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "sample": f"6 full 1436x992/145 frames, whole pipeline, integer mode, OpenMP over rows on "
                       f"{cores} threads",
@@ -226,7 +235,10 @@ def cpu_baseline_leg():
                               "sample": "2 full frames, whole pipeline, integer mode, one thread"},
             "fp64": {"value": fp64, "unit": "frames/s", "cores": cores,
                      "sample": f"2 full frames: grey, downscale, census and arms, then the cost, both "
-                               f"aggregations and the WTA of both bases in FP64 on {cores} threads"}}
+                               f"aggregations and the WTA of both bases in FP64 on {cores} threads"},
+            "small_config": {"workload": "360x248 RGB pair, Dmax 36, no downscaling, whole pipeline, integer mode",
+                             "value": small_all, "unit": "frames/s", "cores": cores,
+                             "single_thread": small_one, "sample": "20 frames on every core, 5 on one thread"}}
 
 
 BATCH_MENU = [(640, 480, 64), (1024, 768, 96), (1436, 992, 145), (1920, 1080, 192)]
