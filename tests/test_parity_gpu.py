@@ -135,6 +135,8 @@ def test_full_vertical_arms_every_tile(tile):
     (600, 90, 300, 1),   # D = 150 after halving, wider than many strips
     (268, 67, 20, 1),    # fused grey + downscale: W = 8k + 4, odd H (last row's grey)
     (16, 3, 5, 1),       # fused grey + downscale: one output row, odd H
+    (8192, 6, 20, 1),    # widest input: processed width 4096, the refine kernel's largest shared memory
+    (4096, 3, 10, 0),    # processed width 4096 without downscaling (row kernel)
 ])
 def test_edge_shapes(W, H, dmax, ds):
     s = scenes.make_scene(W, H, dmax, planes=3, seed=W * 7 + H)
