@@ -1,8 +1,9 @@
 // Preprocessing kernels: grey conversion (Sec. III step 1), 2x mean-pool
 // downscale (Sec. III-A, Eq. 2), and the per-pixel support data of the fused
 // kernel: mini-census code (Sec. III-B) and the four cross arms (Sec. III-C).
-// All of these are memory-bound passes over a few MB; each pixel is read from
-// HBM once and the neighbourhoods are staged in shared memory.
+// These are short passes over a few MB: each pixel is read from HBM once,
+// the grey + downscale pass keeps its neighbourhoods in registers and the
+// support pass stages them in shared memory.
 #include "internal.cuh"
 
 namespace stereo {

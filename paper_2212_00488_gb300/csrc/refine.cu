@@ -9,7 +9,7 @@ namespace stereo {
 namespace {
 
 constexpr int kRefNT = 256;
-constexpr int kMaxRefineX = 4096;   // processed width limit of the row kernel
+constexpr int kMaxRefineX = 4096;   // processed width limit of both refine kernels
 constexpr int kRefLoads = 4;        // rows up to kRefNT * kRefLoads wide load in one round
 
 __device__ __forceinline__ int med3(int a, int b, int c)
