@@ -197,11 +197,13 @@ STEREO_API int stereo_last_launch_count(const stereo_ctx *ctx);
  * 2: 104x4 32-bit for wx up to 26, 3: 104x4 32-bit for wx up to 58,
  * 4: 64x4 16-bit, 5: 100x4 16-bit with 12 row-prefix producer warps
  * instead of 8, 6: 48x8 32-bit (slabs of 8 disparities, two threads per
- * column), 7: 88x4 32-bit for wx up to 141 (the wide windows of Table I).
+ * column), 7: 64x4 32-bit for wx up to 174 with 8 producer warps (the wide
+ * windows of Table I, up to the library's limit of 141), 8: 88x4 32-bit for
+ * wx up to 66 with 8 producer warps.
  * 16-bit row prefixes need max(2*wx+1, 7) times the largest matching cost
  * below 2^16. Every shape gives the same result; they differ only in speed.
  * A compute with a shape that does not fit the parameters fails with EINVAL. */
-#define STEREO_NUM_TILES 8
+#define STEREO_NUM_TILES 9
 
 /* Fixes the tile shape used by later computes on this context (-1 = pick
  * automatically from the frame shape and the SM count, the default).

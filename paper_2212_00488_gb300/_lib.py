@@ -192,7 +192,7 @@ def stereo_last_launch_count(ctx):
     return load().stereo_last_launch_count(ctx)
 
 
-NUM_TILES = 8
+NUM_TILES = 9
 
 
 def stereo_set_tile(ctx, tile):

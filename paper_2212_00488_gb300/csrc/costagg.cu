@@ -615,9 +615,12 @@ using T5 = Tile<100, 4, 5, 12, true, 4, 12>;
 // slabs of 8 disparities: two threads per column, 32-bit prefixes (the
 // batch autotuner's deeper slab)
 using T6 = Tile<48, 8, 5, 4, false, 4, 4>;
-// wide horizontal windows (Table I: W_x up to 141 per side), wx <= 162,
-// 32-bit prefixes
-using T7 = Tile<88, 4, 13, 4, false, 4, 4>;
+// wide horizontal windows (Table I: W_x up to 141 per side), wx <= 174,
+// 32-bit prefixes; 64 columns leave room for 8 producer warps and row slots
+using T7 = Tile<64, 4, 13, 8, false, 4, 8>;
+// wx up to 66 (Table I's W_x = 61) with 32-bit prefixes: 7 prefix entries
+// per producer lane leave room for 8 producer warps and row slots
+using T8 = Tile<88, 4, 7, 8, false, 4, 8>;
 
 template <class T> struct Tag { using type = T; };
 
@@ -634,10 +637,11 @@ bool with_tile(int id, F &&f)
     case 5: f(Tag<T5>{}); return true;
     case 6: f(Tag<T6>{}); return true;
     case 7: f(Tag<T7>{}); return true;
+    case 8: f(Tag<T8>{}); return true;
     default: return false;
     }
 }
-static_assert(kNumTiles == 8, "tile ids 0..7");
+static_assert(kNumTiles == 9, "tile ids 0..8");
 
 template <class T>
 bool fits(const CostAggArgs &a)

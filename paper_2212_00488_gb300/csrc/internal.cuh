@@ -74,7 +74,7 @@ cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, si
 }
 
 // Number of tile shapes of the fused kernel (ids 0 .. kNumTiles-1).
-constexpr int kNumTiles = 8;
+constexpr int kNumTiles = 9;
 int costagg_pick(const CostAggArgs &a, int nsm);
 bool costagg_fits(const CostAggArgs &a, int tile);
 
