@@ -203,8 +203,9 @@ __global__ void __launch_bounds__(kRefNT) refine_kernel(
 //  * along y: full-res row 2y takes low-res row y, row 2y + 1 the mean of
 //    rows y and y + 1 (row y at the last row).
 // Every row the CTA reads is requested in one round of loads; the nearest
-// GCPs of the three rows come from one block scan over their concatenation. The maps, medians and filled rows of low-res rows by and
-// by + 1 are written for the debug and map outputs.
+// GCPs of the three rows come from one block scan over their concatenation.
+// The maps, medians and filled rows of low-res rows by and by + 1 are
+// written for the debug and map outputs.
 constexpr int kRUNT = 256;                 // threads of a CTA
 constexpr int kRULoad = 3;                 // columns per thread in one round of loads
 
