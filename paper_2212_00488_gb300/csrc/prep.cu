@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kGDT) grey_down_kernel(
     uint8_t *__restrict__ s_l, uint8_t *__restrict__ s_r, int W, int H, int ncol, int nband)
 {
     pdl_trigger();
+    pdl_wait();   // launched early behind the previous frame's last kernel, which still reads gf and s
     const bool right = blockIdx.y != 0;
     const int t0 = blockIdx.x * kGDT + threadIdx.x;
     const int nthr = ncol * nband;
@@ -481,9 +482,8 @@ cudaError_t launch_grey_down(const uint8_t *rgb_l, const uint8_t *rgb_r, uint8_t
     const int ncol = W / 4, nband = ((H + 1) / 2 + kGDB - 1) / kGDB;
     const long nthr = (long)ncol * nband;
     dim3 grid((unsigned)((nthr + kGDT - 1) / kGDT), 2);
-    grey_down_kernel<<<grid, kGDT, 0, s>>>(rgb_l, rgb_r, gf_l, s_l, s_r, W, H, ncol, nband);
     *launches += 1;
-    return cudaGetLastError();
+    return launch_dependent(grey_down_kernel, grid, dim3(kGDT), 0, s, rgb_l, rgb_r, gf_l, s_l, s_r, W, H, ncol, nband);
 }
 
 cudaError_t launch_support(const uint8_t *g_l, const uint8_t *g_r, uint32_t *pix_l, uint32_t *pix_r,
